@@ -1,0 +1,201 @@
+/*
+ * cp.h -- C ABI of the GB300 (sm_103a) correntropy kernelized periodogram.
+ *
+ * The library evaluates, for a ragged batch of irregularly sampled
+ * lightcurves, the normalized correntropy kernelized periodogram of
+ * Protopapas et al., arXiv:1412.1840:
+ *
+ *   CKP(f)  = (1/N^2) sum_i sum_j (G_sy(y_i - y_j) - IP) G^P_st(f, t_i - t_j)   Eq. (HP)
+ *   IP      = (1/N^2) sum_i sum_j G_sy(y_i - y_j)                               Eq. (IP)
+ *   nCKP(f) = sqrt(N st) / IP * CKP(f)                                          Eq. (CKP)
+ *
+ * with the Gaussian kernel G_s(x) = exp(-x^2/(2 s^2)) / (sqrt(2 pi) s)
+ * (Eq. (Gausskernel)) and the periodic kernel
+ * G^P_s(f, dt) = exp(-2 sin^2(pi f dt) / s^2) / (sqrt(2 pi) s)
+ * (Eq. (periodickernel)); sy = med(e) (Eq. (pavlosrule)); st fixed, per
+ * curve, or from the Bowley-skewness rule of Section 3.  The best period is
+ * the argmax of nCKP over the trial frequencies (Section 3), and a curve is
+ * labelled periodic when nCKP(best) exceeds th(pSNR) of Table tab:th with
+ * pSNR = 0.7413 iqr(y) / (alpha med(e)) (Eq. (pSNR), Section 4.1).
+ *
+ * All entry points return a cp_status and never throw.  On failure
+ * cp_last_error() returns a thread-local message.  Nothing is computed on
+ * the CPU: every step of the method runs in CUDA kernels on the plan's
+ * device; a missing or unusable device is an error (CP_ECUDA).
+ */
+#ifndef CP_H
+#define CP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CP_OK = 0,
+    CP_EINVAL = 1,       /* invalid argument or input value (see cp_last_error)      */
+    CP_ENOMEM = 2,       /* device or pinned host allocation failed                  */
+    CP_ECUDA = 3,        /* CUDA runtime / driver error                              */
+    CP_ETIMEOUT = 4,     /* a bounded device wait gave up (reserved; no waits today) */
+    CP_ESTATE = 5,       /* plan used in a state that does not allow the call        */
+    CP_EUNSUPPORTED = 6  /* valid request the build does not support (e.g. N > max)  */
+} cp_status;
+
+typedef struct cp_plan_s *cp_plan_t;
+
+/* Evaluation form. */
+enum { CP_FORM_DIRECT = 0, /* FP32 pair sum, FP64-exact fixed-point phases          */
+       CP_FORM_TENSOR = 1  /* Fourier/Bessel series, FP16/BF16 tcgen05 GEMMs        */ };
+enum { CP_DTYPE_FP16 = 0, CP_DTYPE_BF16 = 1 };
+/* How sigma_t is chosen per curve. */
+enum { CP_SIGMA_T_FIXED = 0,     /* options.sigma_t for every curve                    */
+       CP_SIGMA_T_PER_CURVE = 1, /* options.sigma_t_per_curve[c] (host array)          */
+       CP_SIGMA_T_RULE = 2       /* 0.1 + 0.5 exp(-12 S^2), S = Bowley skewness of y   */ };
+/* Where times / mags / errs live. */
+enum { CP_MEM_HOST = 0, CP_MEM_DEVICE = 1 };
+
+/*
+ * Trial frequencies (1/day).  The uniform grid is f_k = f_min + k*df,
+ * k = 0..n_freq-1, each computed in FP64 (not accumulated); it spans
+ * [f_min, f_max] with f_max = f_min + (n_freq-1)*df.
+ *
+ * hierarchical != 0 makes cp_best_period run the coarse-then-fine search:
+ * coarse grid f_min + k*coarse_df over [f_min, f_max]; the top_k local
+ * maxima (v[k] > v[k-1] and v[k] >= v[k+1], ends compared with their single
+ * neighbour; ties to the lower k); each refined on f_peak + j*fine_df,
+ * |j| <= J = round(fine_halfwidth / fine_df), points outside [f_min, f_max]
+ * skipped; the best over all refined candidates by value, ties to the lower
+ * candidate index rank*(2J+1) + (j+J).  cp_periodogram always evaluates the
+ * uniform grid.
+ */
+typedef struct {
+    double f_min;
+    double df;
+    int64_t n_freq;
+    int32_t hierarchical;
+    int32_t top_k;
+    double coarse_df;
+    double fine_df;
+    double fine_halfwidth;
+} cp_freq_grid;
+
+typedef struct {
+    int32_t sigma_t_mode;            /* CP_SIGMA_T_*                                    */
+    float sigma_t;                   /* fixed kernel size (mode FIXED)                  */
+    const float *sigma_t_per_curve;  /* host, n_curves values (mode PER_CURVE); copied  */
+    float alpha;                     /* error-bar correction factor of Eq. (pSNR), >0   */
+    int32_t form;                    /* CP_FORM_*                                       */
+    int32_t dtype;                   /* CP_DTYPE_* (tensor form only)                   */
+    int32_t n_max;                   /* harmonics of the tensor form; 0 = per curve,    */
+                                     /* smallest n with truncation tail <= 1e-4         */
+    int32_t input_memory;            /* CP_MEM_HOST or CP_MEM_DEVICE                    */
+    int32_t use_graph;               /* capture cp_best_period's step in a CUDA graph   */
+    int32_t device;                  /* CUDA device ordinal                             */
+} cp_options;
+
+/* Fills defaults: FIXED sigma_t = 0.3, alpha = 1, DIRECT form, FP16,
+ * n_max = 0, HOST inputs, graphs on, device 0. */
+void cp_default_options(cp_options *opt);
+
+/*
+ * cp_plan -- validate a ragged lightcurve batch, allocate device buffers,
+ * and bind the input arrays to a new plan.
+ *
+ *   times   FP64 observation times (days), sum N values, curve c occupies
+ *           [offsets[c], offsets[c+1]); any order within a curve.
+ *   mags    FP32 magnitudes, same layout.
+ *   errs    FP32 error bars (> 0 median per curve), same layout.
+ *   offsets HOST int64 array of n_curves+1 entries: offsets[0] = 0, each
+ *           curve holds 2 <= N <= cp_max_points() samples.
+ *   grid, opt  as above (opt NULL = defaults).
+ *   cuda_stream  cudaStream_t the plan runs on (NULL = legacy default stream).
+ *
+ * times/mags/errs are host or device pointers as opt->input_memory says.
+ * The plan keeps the POINTERS, not copies: every cp_periodogram /
+ * cp_best_period call reads their current contents (host arrays are copied
+ * to the device inside the call), so the caller keeps them alive and
+ * unchanged in size until cp_destroy.  Non-finite values and a zero median
+ * error are reported by the call that reads them (CP_EINVAL).
+ * offsets, grid, options and sigma_t_per_curve are copied at plan time.
+ * The plan owns its device memory until cp_destroy.  A plan is used by one
+ * host thread at a time.
+ */
+cp_status cp_plan(const double *times, const float *mags, const float *errs,
+                  const int64_t *offsets, int64_t n_curves, const cp_freq_grid *grid,
+                  const cp_options *opt, void *cuda_stream, cp_plan_t *out_plan);
+
+/*
+ * cp_periodogram -- nCKP of every curve on the uniform grid, Eq. (CKP).
+ *   out  DEVICE float array, n_curves x n_freq, row-major in the caller's
+ *        curve order (row c = curve c); may be NULL to only run the pass.
+ * Asynchronous on the plan's stream; cp_sync() reports input errors.
+ */
+cp_status cp_periodogram(cp_plan_t plan, float *out);
+
+/*
+ * cp_best_period -- best frequency, its nCKP and the discriminator of
+ * Section 4.1 for every curve (full grid or coarse-then-fine per the grid).
+ * All outputs are HOST arrays of n_curves entries in the caller's curve
+ * order; any may be NULL.
+ *   best_idx   full grid: k of the best frequency; hierarchical: candidate
+ *              index rank*(2J+1) + (j+J)
+ *   best_freq  FP64 best frequency (1/day); best period = 1/best_freq
+ *   best_stat  nCKP at the best frequency
+ *   is_periodic  1 if best_stat > th(pSNR bin) of Table tab:th
+ *   psnr       pSNR of Eq. (pSNR)
+ * Synchronous: returns after the results are on the host.
+ */
+cp_status cp_best_period(cp_plan_t plan, int64_t *best_idx, double *best_freq, float *best_stat,
+                         uint8_t *is_periodic, float *psnr);
+
+/* Waits for the plan's stream and returns the device-side status of the
+ * last call (CP_EINVAL for non-finite inputs or a zero median error). */
+cp_status cp_sync(cp_plan_t plan);
+
+/*
+ * cp_curve_stats -- per-curve scalars of the last call, HOST arrays of
+ * n_curves (any may be NULL): sigma_y = med(e) (Eq. (pavlosrule)), the
+ * sigma_t used, IP of Eq. (IP), pSNR of Eq. (pSNR).  Synchronous.
+ */
+cp_status cp_curve_stats(cp_plan_t plan, float *sigma_y, float *sigma_t, double *ip, float *psnr);
+
+/* Work and timing of the plan (for throughput and roofline reports). */
+typedef struct {
+    int64_t n_curves;
+    int64_t n_points;             /* sum N                                             */
+    double pair_freq_full;        /* sum_c N(N-1)/2 * n_freq: one uniform-grid pass     */
+    double pair_freq_search;      /* pair-frequency evaluations of one cp_best_period   */
+    int64_t launches_per_search;  /* kernels one cp_best_period launches                */
+    float last_pair_kernel_ms;    /* device time of the pair-sum kernel(s), last call   */
+    float last_step_ms;           /* device time of the whole last cp_best_period       */
+    int32_t n_sm;                 /* SMs of the plan's device                           */
+    int32_t max_n;                /* largest N in the batch                             */
+} cp_plan_info;
+
+cp_status cp_get_plan_info(cp_plan_t plan, cp_plan_info *info);
+
+/* Releases the plan's device and pinned host memory (NULL is a no-op). */
+void cp_destroy(cp_plan_t plan);
+
+/* Largest N per curve the build supports. */
+int64_t cp_max_points(void);
+
+/*
+ * cp_bessel_coefficients -- Fourier coefficients of the periodic kernel
+ * used by the tensor form: exp(-2 sin^2(x)/s^2) = a_0 + sum_n a_n cos(2 n x)
+ * with a_0 = e^-k I_0(k), a_n = 2 e^-k I_n(k), k = 1/s^2 (Eq. (taylor)
+ * regrouped by harmonic).  Writes a_0..a_n_max to out (host, n_max+1).
+ * Computed in FP64 by the trapezoid rule on (1/pi) int_0^pi e^{k(cos t - 1)} cos(n t) dt.
+ */
+cp_status cp_bessel_coefficients(double sigma_t, int32_t n_max, double *out);
+
+const char *cp_status_string(cp_status s);
+const char *cp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CP_H */

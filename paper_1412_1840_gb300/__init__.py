@@ -1,0 +1,282 @@
+"""GB300 (sm_103a) correntropy kernelized periodogram of arXiv:1412.1840.
+
+Thin Python binding of the C ABI in ``include/cp.h`` (library
+``_lib/libcp.so``).  It only marshals arguments: every step of the method
+runs in the library's CUDA kernels.  There is no CPU fallback; if the
+library cannot be loaded or no CUDA device is present, calls raise.
+
+Entry points carry the C names: ``cp_plan``, ``cp_periodogram``,
+``cp_best_period``, ``cp_sync``, ``cp_curve_stats``, ``cp_get_plan_info``,
+``cp_destroy``, ``cp_bessel_coefficients``, ``cp_max_points``.  ``Plan`` wraps
+a plan handle and keeps the bound input arrays alive.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libcp.so")
+
+CP_OK, CP_EINVAL, CP_ENOMEM, CP_ECUDA, CP_ETIMEOUT, CP_ESTATE, CP_EUNSUPPORTED = range(7)
+CP_FORM_DIRECT, CP_FORM_TENSOR = 0, 1
+CP_DTYPE_FP16, CP_DTYPE_BF16 = 0, 1
+CP_SIGMA_T_FIXED, CP_SIGMA_T_PER_CURVE, CP_SIGMA_T_RULE = 0, 1, 2
+CP_MEM_HOST, CP_MEM_DEVICE = 0, 1
+
+
+class CpError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__("%s: status %d (%s): %s" % (where, status, _status_name(status), msg))
+        self.status = status
+
+
+class cp_freq_grid(ctypes.Structure):
+    _fields_ = [("f_min", ctypes.c_double), ("df", ctypes.c_double), ("n_freq", ctypes.c_int64),
+                ("hierarchical", ctypes.c_int32), ("top_k", ctypes.c_int32), ("coarse_df", ctypes.c_double),
+                ("fine_df", ctypes.c_double), ("fine_halfwidth", ctypes.c_double)]
+
+
+class cp_options(ctypes.Structure):
+    _fields_ = [("sigma_t_mode", ctypes.c_int32), ("sigma_t", ctypes.c_float),
+                ("sigma_t_per_curve", ctypes.POINTER(ctypes.c_float)), ("alpha", ctypes.c_float),
+                ("form", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n_max", ctypes.c_int32),
+                ("input_memory", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class cp_plan_info(ctypes.Structure):
+    _fields_ = [("n_curves", ctypes.c_int64), ("n_points", ctypes.c_int64), ("pair_freq_full", ctypes.c_double),
+                ("pair_freq_search", ctypes.c_double), ("launches_per_search", ctypes.c_int64),
+                ("last_pair_kernel_ms", ctypes.c_float), ("last_step_ms", ctypes.c_float),
+                ("n_sm", ctypes.c_int32), ("max_n", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        L.cp_default_options.argtypes = [ctypes.POINTER(cp_options)]
+        L.cp_default_options.restype = None
+        L.cp_plan.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(cp_freq_grid), ctypes.POINTER(cp_options), vp,
+                              ctypes.POINTER(vp)]
+        L.cp_periodogram.argtypes = [vp, vp]
+        L.cp_best_period.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.cp_sync.argtypes = [vp]
+        L.cp_curve_stats.argtypes = [vp, vp, vp, vp, vp]
+        L.cp_get_plan_info.argtypes = [vp, ctypes.POINTER(cp_plan_info)]
+        L.cp_destroy.argtypes = [vp]
+        L.cp_destroy.restype = None
+        L.cp_max_points.restype = i64
+        L.cp_bessel_coefficients.argtypes = [d, ctypes.c_int32, vp]
+        L.cp_status_string.argtypes = [ctypes.c_int]
+        L.cp_status_string.restype = ctypes.c_char_p
+        L.cp_last_error.restype = ctypes.c_char_p
+        for fn in ("cp_plan", "cp_periodogram", "cp_best_period", "cp_sync", "cp_curve_stats",
+                   "cp_get_plan_info", "cp_bessel_coefficients"):
+            getattr(L, fn).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def lib():
+    return _load()
+
+
+def _status_name(s: int) -> str:
+    try:
+        return _load().cp_status_string(s).decode()
+    except Exception:
+        return str(s)
+
+
+def _check(status: int, where: str):
+    if status != CP_OK:
+        raise CpError(status, where, (_load().cp_last_error() or b"").decode())
+
+
+def _ptr(a):
+    """(pointer, on_device, keepalive) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, False, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), bool(a.is_cuda), a
+    arr = np.ascontiguousarray(a)
+    return arr.ctypes.data, False, arr
+
+
+def cp_default_options() -> cp_options:
+    o = cp_options()
+    _load().cp_default_options(ctypes.byref(o))
+    return o
+
+
+def cp_max_points() -> int:
+    return int(_load().cp_max_points())
+
+
+def cp_bessel_coefficients(sigma_t: float, n_max: int) -> np.ndarray:
+    out = np.zeros(n_max + 1, dtype=np.float64)
+    _check(_load().cp_bessel_coefficients(float(sigma_t), int(n_max), out.ctypes.data), "cp_bessel_coefficients")
+    return out
+
+
+def make_grid(f_min, df, n_freq, hierarchical=False, coarse_df=0.0, top_k=0, fine_df=0.0, fine_halfwidth=0.0):
+    return cp_freq_grid(float(f_min), float(df), int(n_freq), int(bool(hierarchical)), int(top_k),
+                        float(coarse_df), float(fine_df), float(fine_halfwidth))
+
+
+class Plan:
+    """A cp_plan handle bound to a CSR lightcurve batch.
+
+    times (float64), mags and errs (float32) are numpy arrays or torch
+    tensors, all on the host or all on one CUDA device; offsets is a host
+    int64 array of n_curves + 1 entries.  The arrays are kept alive by the
+    plan, and every call reads their current contents."""
+
+    def __init__(self, times, mags, errs, offsets, grid: cp_freq_grid, sigma_t=0.3, sigma_t_mode=None,
+                 sigma_t_per_curve=None, alpha=1.0, form=CP_FORM_DIRECT, dtype=CP_DTYPE_FP16, n_max=0,
+                 use_graph=True, device=None, stream=None):
+        L = _load()
+        pt, dev_t, kt = _ptr(times)
+        pm, dev_m, km = _ptr(mags)
+        pe, dev_e, ke = _ptr(errs)
+        if not (dev_t == dev_m == dev_e):
+            raise ValueError("times, mags and errs must all be on the host or all on the device")
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        self._keep = [kt, km, ke, off]
+        o = cp_default_options()
+        if sigma_t_mode is None:
+            sigma_t_mode = CP_SIGMA_T_PER_CURVE if sigma_t_per_curve is not None else CP_SIGMA_T_FIXED
+        o.sigma_t_mode = int(sigma_t_mode)
+        o.sigma_t = float(sigma_t)
+        if sigma_t_per_curve is not None:
+            stpc = np.ascontiguousarray(np.asarray(sigma_t_per_curve, dtype=np.float32))
+            self._keep.append(stpc)
+            o.sigma_t_per_curve = stpc.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        o.alpha = float(alpha)
+        o.form = int(form)
+        o.dtype = int(dtype)
+        o.n_max = int(n_max)
+        o.input_memory = CP_MEM_DEVICE if dev_t else CP_MEM_HOST
+        o.use_graph = 1 if use_graph else 0
+        if device is None:
+            device = times.device.index if dev_t and times.device.index is not None else 0
+        o.device = int(device)
+        if stream is None and dev_t:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.stream = stream
+        self.n_curves = int(off.shape[0] - 1)
+        self.grid = grid
+        h = ctypes.c_void_p()
+        _check(L.cp_plan(pt, pm, pe, off.ctypes.data, self.n_curves, ctypes.byref(grid), ctypes.byref(o),
+                         ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)), "cp_plan")
+        self.handle = h
+
+    # -- entry points ---------------------------------------------------------
+    def periodogram(self, out=None):
+        """Runs the uniform-grid pass; ``out`` is a CUDA float32 tensor
+        [n_curves, n_freq] (or None).  Asynchronous on the plan's stream."""
+        p = None
+        if out is not None:
+            p, on_dev, _ = _ptr(out)
+            if not on_dev:
+                raise ValueError("out must be a CUDA tensor")
+        _check(_load().cp_periodogram(self.handle, p), "cp_periodogram")
+        return out
+
+    def best_period(self):
+        n = self.n_curves
+        idx = np.empty(n, np.int64); f = np.empty(n, np.float64); v = np.empty(n, np.float32)
+        per = np.empty(n, np.uint8); ps = np.empty(n, np.float32)
+        _check(_load().cp_best_period(self.handle, idx.ctypes.data, f.ctypes.data, v.ctypes.data, per.ctypes.data,
+                                      ps.ctypes.data), "cp_best_period")
+        return {"best_idx": idx, "best_freq": f, "best_stat": v, "is_periodic": per.astype(bool), "psnr": ps}
+
+    def best_period_into(self, idx, f, v, per, ps):
+        """Same as best_period, writing into caller-provided host numpy arrays."""
+        _check(_load().cp_best_period(self.handle, idx.ctypes.data, f.ctypes.data, v.ctypes.data, per.ctypes.data,
+                                      ps.ctypes.data), "cp_best_period")
+
+    def sync(self):
+        _check(_load().cp_sync(self.handle), "cp_sync")
+
+    def curve_stats(self):
+        n = self.n_curves
+        sy = np.empty(n, np.float32); st = np.empty(n, np.float32); ip = np.empty(n, np.float64)
+        ps = np.empty(n, np.float32)
+        _check(_load().cp_curve_stats(self.handle, sy.ctypes.data, st.ctypes.data, ip.ctypes.data, ps.ctypes.data),
+               "cp_curve_stats")
+        return {"sigma_y": sy, "sigma_t": st, "ip": ip, "psnr": ps}
+
+    def info(self) -> dict:
+        i = cp_plan_info()
+        _check(_load().cp_get_plan_info(self.handle, ctypes.byref(i)), "cp_get_plan_info")
+        return {k: getattr(i, k) for k, _ in cp_plan_info._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _load().cp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def cp_plan(times, mags, errs, offsets, grid, **kw) -> Plan:
+    return Plan(times, mags, errs, offsets, grid, **kw)
+
+
+def cp_periodogram(plan: Plan, out=None):
+    return plan.periodogram(out)
+
+
+def cp_best_period(plan: Plan):
+    return plan.best_period()
+
+
+def cp_sync(plan: Plan):
+    plan.sync()
+
+
+def cp_curve_stats(plan: Plan):
+    return plan.curve_stats()
+
+
+def cp_get_plan_info(plan: Plan):
+    return plan.info()
+
+
+def cp_destroy(plan: Plan):
+    plan.close()
+
+
+def grid_from(g) -> cp_freq_grid:
+    """cp_freq_grid from any object with the synthetic-grid attribute names."""
+    return make_grid(g.f_min, g.df, g.n_freq, g.hierarchical, g.coarse_df, g.top_k, g.fine_df, g.fine_halfwidth)

@@ -1,0 +1,863 @@
+// cp_api.cu -- host side of the C ABI declared in include/cp.h.
+//
+// A plan binds a ragged CSR lightcurve batch (arXiv:1412.1840, Section 5.1:
+// one file of (t, magnitude, error) per star) and a trial-frequency grid to
+// device buffers, a longest-first work schedule and, optionally, a captured
+// CUDA graph of one best-period search.  All arithmetic of the method runs in
+// the kernels of cp_kernels.cu; this file only validates, schedules, allocates
+// and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "cp.h"
+#include "cp_internal.cuh"
+
+using namespace cpk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cp_status fail(cp_status s, const std::string& msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+// A failed runtime call also sets the runtime's per-thread last error; it is
+// cleared here so that it cannot surface later in unrelated CUDA code.
+#define CP_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            cudaGetLastError();                                                         \
+            return fail(e_ == cudaErrorMemoryAllocation ? CP_ENOMEM : CP_ECUDA,         \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));            \
+        }                                                                               \
+    } while (0)
+
+// Entry-point epilogue: a pending runtime error that no CP_CUDA check saw is
+// reported (and cleared) instead of being left behind.
+static cp_status finish(cp_status st, const char* where)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (st == CP_OK && e != cudaSuccess)
+        return fail(CP_ECUDA, std::string(where) + ": pending CUDA error " + cudaGetErrorString(e));
+    return st;
+}
+
+struct Wave {
+    int slot_begin, slot_end;
+    int64_t tile_begin, tile_end;
+};
+
+struct PairLaunch {
+    int stage;
+    int wave;
+};
+
+}  // namespace
+
+struct cp_plan_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    int n_sm = 0;
+
+    const double* times = nullptr;
+    const float* mags = nullptr;
+    const float* errs = nullptr;
+    bool host_inputs = true;
+    bool host_pinned = false;
+
+    int64_t n_curves = 0, n_points = 0;
+    std::vector<int64_t> offsets;
+    cp_freq_grid grid{};
+    cp_options opt{};
+    int max_n = 0, np2max = 1;
+    int64_t kc = 0;   // coarse grid points
+    int J = 0;        // fine half-width in steps
+    double f_max = 0;
+
+    std::vector<int32_t> order;          // slot -> curve
+    std::vector<int32_t> fc;             // per curve
+    std::vector<int64_t> unit_full, unit_coarse, unit_fine, wtile;
+    std::vector<Wave> waves;
+    size_t pair_smem = 0;
+    int pair_grid = 0;
+
+    // device buffers
+    void* dblock = nullptr;              // one allocation for everything below
+    double* d_times = nullptr;
+    float* d_mags = nullptr;
+    float* d_errs = nullptr;
+    CurveParams* d_cp = nullptr;
+    float* d_yp = nullptr;
+    uint64_t *d_ph_base = nullptr, *d_ph_full = nullptr, *d_ph_coarse = nullptr, *d_ph_fine = nullptr;
+    float* d_stpc = nullptr;
+    int32_t* d_order = nullptr;
+    int64_t *d_unit_full = nullptr, *d_unit_coarse = nullptr, *d_unit_fine = nullptr, *d_wtile = nullptr;
+    float* d_W = nullptr;
+    float* d_coarse = nullptr;
+    int32_t *d_peaks = nullptr, *d_npeaks = nullptr;
+    unsigned long long* d_u64 = nullptr;  // [status | best_key (n_curves) | queues]
+    int64_t n_u64 = 0;
+    int64_t* d_res_idx = nullptr;
+    double* d_res_freq = nullptr;
+    float* d_res_stat = nullptr;
+    uint8_t* d_res_per = nullptr;
+    float* d_res_psnr = nullptr;
+
+    // pinned host
+    void* hblock = nullptr;
+    int64_t* h_res_idx = nullptr;
+    double* h_res_freq = nullptr;
+    float* h_res_stat = nullptr;
+    uint8_t* h_res_per = nullptr;
+    float* h_res_psnr = nullptr;
+    unsigned long long* h_status = nullptr;
+    double* h_times = nullptr;             // pinned staging for pageable host inputs
+    float* h_mags = nullptr;
+    float* h_errs = nullptr;
+
+    // graph and timing
+    cudaGraphExec_t exec = nullptr;
+    bool graph_ready = false;
+    std::vector<cudaEvent_t> ev_pair;      // 2 per pair launch of a search
+    cudaEvent_t ev_step0 = nullptr, ev_step1 = nullptr;
+    float last_pair_ms = 0.f, last_step_ms = 0.f;
+    int64_t launches_per_search = 0;
+    double pf_full = 0, pf_search = 0;
+    bool ran = false;
+    bool capturing = false;   // inside build_graph's stream capture
+};
+
+namespace {
+
+inline unsigned long long* status_word(cp_plan_t p) { return p->d_u64; }
+inline unsigned long long* best_keys(cp_plan_t p) { return p->d_u64 + 1; }
+inline unsigned long long* queue_word(cp_plan_t p, int i) { return p->d_u64 + 1 + p->n_curves + i; }
+
+// Events recorded during capture must be external nodes to stay timeable;
+// outside capture the flag is not allowed.
+unsigned rec_flags(cp_plan_t p) { return p->capturing ? cudaEventRecordExternal : cudaEventRecordDefault; }
+
+int fc_for(int n)
+{
+    const int npad = (n + kTile - 1) / kTile * kTile;
+    int f = kFcMax;
+    while (f > 2 && (size_t)npad * f * 12 > (size_t)kTableBytes) f >>= 1;
+    return f;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Copies host inputs (pageable case) into the pinned staging buffers.
+void stage_host_inputs(cp_plan_t p)
+{
+    if (p->host_inputs && !p->host_pinned) {
+        std::memcpy(p->h_times, p->times, (size_t)p->n_points * sizeof(double));
+        std::memcpy(p->h_mags, p->mags, (size_t)p->n_points * sizeof(float));
+        std::memcpy(p->h_errs, p->errs, (size_t)p->n_points * sizeof(float));
+    }
+}
+
+cp_status enqueue_inputs(cp_plan_t p, cudaStream_t s)
+{
+    if (!p->host_inputs) return CP_OK;
+    const double* st = p->host_pinned ? p->times : p->h_times;
+    const float* sm = p->host_pinned ? p->mags : p->h_mags;
+    const float* se = p->host_pinned ? p->errs : p->h_errs;
+    CP_CUDA(cudaMemcpyAsync(p->d_times, st, (size_t)p->n_points * sizeof(double), cudaMemcpyHostToDevice, s));
+    CP_CUDA(cudaMemcpyAsync(p->d_mags, sm, (size_t)p->n_points * sizeof(float), cudaMemcpyHostToDevice, s));
+    CP_CUDA(cudaMemcpyAsync(p->d_errs, se, (size_t)p->n_points * sizeof(float), cudaMemcpyHostToDevice, s));
+    return CP_OK;
+}
+
+cp_status enqueue_stats(cp_plan_t p, cudaStream_t s)
+{
+    CP_CUDA(launch_zero_u64(p->d_u64, p->n_u64, s));
+    StatsArgs a{};
+    a.times = p->host_inputs ? p->d_times : p->times;
+    a.mags = p->host_inputs ? p->d_mags : p->mags;
+    a.errs = p->host_inputs ? p->d_errs : p->errs;
+    a.cp = p->d_cp;
+    a.yp = p->d_yp;
+    a.ph_base = p->d_ph_base;
+    a.ph_full = p->d_ph_full;
+    a.ph_coarse = p->d_ph_coarse;
+    a.ph_fine = p->d_ph_fine;
+    a.sigma_t_per_curve = p->d_stpc;
+    a.f_min = p->grid.f_min;
+    a.df = p->grid.df;
+    a.coarse_df = p->grid.coarse_df;
+    a.fine_df = p->grid.fine_df;
+    a.hierarchical = p->grid.hierarchical ? 1 : 0;
+    a.sigma_t_mode = p->opt.sigma_t_mode;
+    a.sigma_t = p->opt.sigma_t;
+    a.alpha = p->opt.alpha;
+    a.np2max = p->np2max;
+    a.status = reinterpret_cast<int*>(status_word(p));
+    CP_CUDA(launch_stats(a, (int)p->n_curves, s));
+    return CP_OK;
+}
+
+PairArgs pair_args(cp_plan_t p, int stage, int w, float* out)
+{
+    const Wave& wv = p->waves[w];
+    PairArgs a{};
+    a.cp = p->d_cp;
+    a.order = p->d_order;
+    a.wtile_start = p->d_wtile;
+    a.W = p->d_W;
+    a.yp = p->d_yp;
+    a.ph_base = p->d_ph_base;
+    a.ph_coarse = p->d_ph_coarse;
+    a.peaks = p->d_peaks;
+    a.n_peaks = p->d_npeaks;
+    a.stage = stage;
+    a.slot_begin = wv.slot_begin;
+    a.slot_end = wv.slot_end;
+    a.wtile_base = wv.tile_begin;
+    a.top_k = p->grid.top_k;
+    a.fine_half = p->J;
+    a.f_min = p->grid.f_min;
+    a.f_max = p->f_max;
+    a.coarse_df = p->grid.coarse_df;
+    a.out = out;
+    a.out_ld = p->grid.n_freq;
+    a.coarse_out = p->d_coarse;
+    a.best_key = best_keys(p);
+    a.queue = queue_word(p, 3 * w + stage);
+    const std::vector<int64_t>* us;
+    if (stage == kStageFull) {
+        a.unit_start = p->d_unit_full;
+        a.ph_step = p->d_ph_full;
+        a.n_freq = p->grid.n_freq;
+        a.step = p->grid.df;
+        us = &p->unit_full;
+    } else if (stage == kStageCoarse) {
+        a.unit_start = p->d_unit_coarse;
+        a.ph_step = p->d_ph_coarse;
+        a.n_freq = p->kc;
+        a.step = p->grid.coarse_df;
+        us = &p->unit_coarse;
+    } else {
+        a.unit_start = p->d_unit_fine;
+        a.ph_step = p->d_ph_fine;
+        a.n_freq = p->kc;
+        a.step = p->grid.fine_df;
+        us = &p->unit_fine;
+    }
+    a.unit_begin = (*us)[wv.slot_begin];
+    a.unit_end = (*us)[wv.slot_end];
+    return a;
+}
+
+cp_status enqueue_wave_w(cp_plan_t p, int w, cudaStream_t s)
+{
+    const Wave& wv = p->waves[w];
+    BuildWArgs b{};
+    b.cp = p->d_cp;
+    b.order = p->d_order;
+    b.wtile_start = p->d_wtile;
+    b.yp = p->d_yp;
+    b.W = p->d_W;
+    b.slot_begin = wv.slot_begin;
+    b.slot_end = wv.slot_end;
+    b.tile_begin = wv.tile_begin;
+    b.tile_end = wv.tile_end;
+    CP_CUDA(launch_build_w(b, s));
+    return CP_OK;
+}
+
+cp_status enqueue_pair(cp_plan_t p, int stage, int w, float* out, cudaStream_t s, int* ev_idx)
+{
+    const PairArgs a = pair_args(p, stage, w, out);
+    if (ev_idx) CP_CUDA(cudaEventRecordWithFlags(p->ev_pair[2 * (*ev_idx)], s, rec_flags(p)));
+    CP_CUDA(launch_pair_direct(a, p->pair_grid, p->pair_smem, s));
+    if (ev_idx) {
+        CP_CUDA(cudaEventRecordWithFlags(p->ev_pair[2 * (*ev_idx) + 1], s, rec_flags(p)));
+        (*ev_idx)++;
+    }
+    return CP_OK;
+}
+
+cp_status enqueue_search(cp_plan_t p, cudaStream_t s)
+{
+    cp_status st;
+    CP_CUDA(cudaEventRecordWithFlags(p->ev_step0, s, rec_flags(p)));
+    if ((st = enqueue_inputs(p, s)) != CP_OK) return st;
+    if ((st = enqueue_stats(p, s)) != CP_OK) return st;
+    int ev = 0;
+    for (int w = 0; w < (int)p->waves.size(); w++) {
+        if ((st = enqueue_wave_w(p, w, s)) != CP_OK) return st;
+        if (!p->grid.hierarchical) {
+            if ((st = enqueue_pair(p, kStageFull, w, nullptr, s, &ev)) != CP_OK) return st;
+        } else {
+            if ((st = enqueue_pair(p, kStageCoarse, w, nullptr, s, &ev)) != CP_OK) return st;
+            TopkArgs t{};
+            t.coarse = p->d_coarse;
+            t.order = p->d_order;
+            t.slot_begin = p->waves[w].slot_begin;
+            t.slot_end = p->waves[w].slot_end;
+            t.n_freq = p->kc;
+            t.top_k = p->grid.top_k;
+            t.peaks = p->d_peaks;
+            t.n_peaks = p->d_npeaks;
+            CP_CUDA(launch_topk(t, s));
+            if ((st = enqueue_pair(p, kStageFine, w, nullptr, s, &ev)) != CP_OK) return st;
+        }
+    }
+    FinalArgs f{};
+    f.cp = p->d_cp;
+    f.best_key = best_keys(p);
+    f.peaks = p->d_peaks;
+    f.n_curves = (int)p->n_curves;
+    f.hierarchical = p->grid.hierarchical ? 1 : 0;
+    f.top_k = p->grid.top_k;
+    f.fine_half = p->J;
+    f.f_min = p->grid.f_min;
+    f.df = p->grid.df;
+    f.coarse_df = p->grid.coarse_df;
+    f.fine_df = p->grid.fine_df;
+    f.best_idx = p->d_res_idx;
+    f.best_freq = p->d_res_freq;
+    f.best_stat = p->d_res_stat;
+    f.is_periodic = p->d_res_per;
+    f.psnr = p->d_res_psnr;
+    CP_CUDA(launch_finalize(f, s));
+    const size_t nc = (size_t)p->n_curves;
+    CP_CUDA(cudaMemcpyAsync(p->h_res_idx, p->d_res_idx, nc * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaMemcpyAsync(p->h_res_freq, p->d_res_freq, nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaMemcpyAsync(p->h_res_stat, p->d_res_stat, nc * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaMemcpyAsync(p->h_res_per, p->d_res_per, nc, cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaMemcpyAsync(p->h_res_psnr, p->d_res_psnr, nc * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaMemcpyAsync(p->h_status, p->d_u64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaEventRecordWithFlags(p->ev_step1, s, rec_flags(p)));
+    return CP_OK;
+}
+
+cp_status build_graph(cp_plan_t p)
+{
+    CP_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    p->capturing = true;
+    cp_status st = enqueue_search(p, p->cap);
+    p->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+    if (st != CP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&p->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    p->graph_ready = true;
+    return CP_OK;
+}
+
+cp_status read_timings(cp_plan_t p)
+{
+    float total = 0.f;
+    const int npl = (int)p->ev_pair.size() / 2;
+    for (int i = 0; i < npl; i++) {
+        float ms = 0.f;
+        CP_CUDA(cudaEventElapsedTime(&ms, p->ev_pair[2 * i], p->ev_pair[2 * i + 1]));
+        total += ms;
+    }
+    p->last_pair_ms = total;
+    float ms = 0.f;
+    CP_CUDA(cudaEventElapsedTime(&ms, p->ev_step0, p->ev_step1));
+    p->last_step_ms = ms;
+    return CP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cp_default_options(cp_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->sigma_t_mode = CP_SIGMA_T_FIXED;
+    o->sigma_t = 0.3f;
+    o->sigma_t_per_curve = nullptr;
+    o->alpha = 1.0f;
+    o->form = CP_FORM_DIRECT;
+    o->dtype = CP_DTYPE_FP16;
+    o->n_max = 0;
+    o->input_memory = CP_MEM_HOST;
+    o->use_graph = 1;
+    o->device = 0;
+}
+
+int64_t cp_max_points(void) { return kMaxN; }
+
+const char* cp_status_string(cp_status s)
+{
+    switch (s) {
+    case CP_OK: return "ok";
+    case CP_EINVAL: return "invalid argument";
+    case CP_ENOMEM: return "out of memory";
+    case CP_ECUDA: return "CUDA error";
+    case CP_ETIMEOUT: return "device wait timed out";
+    case CP_ESTATE: return "invalid plan state";
+    case CP_EUNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+const char* cp_last_error(void) { return g_last_error.c_str(); }
+
+void cp_destroy(cp_plan_t p)
+{
+    if (!p) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    for (cudaEvent_t e : p->ev_pair) cudaEventDestroy(e);
+    if (p->ev_step0) cudaEventDestroy(p->ev_step0);
+    if (p->ev_step1) cudaEventDestroy(p->ev_step1);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->dblock) cudaFree(p->dblock);
+    if (p->hblock) cudaFreeHost(p->hblock);
+    cudaSetDevice(prev);
+    cudaGetLastError();
+    delete p;
+}
+
+static cp_status plan_impl(const double* times, const float* mags, const float* errs,
+                           const int64_t* offsets, int64_t n_curves, const cp_freq_grid* grid,
+                           const cp_options* opt_in, void* stream, cp_plan_s* p)
+{
+    if (!times || !mags || !errs || !offsets || !grid)
+        return fail(CP_EINVAL, "cp_plan: null argument");
+    if (n_curves < 1 || n_curves > (int64_t)1 << 30)
+        return fail(CP_EINVAL, "cp_plan: n_curves must be in [1, 2^30]");
+    cp_options opt;
+    if (opt_in) opt = *opt_in; else cp_default_options(&opt);
+    if (opt.form != CP_FORM_DIRECT)
+        return fail(CP_EUNSUPPORTED, "cp_plan: only the direct form is built in this library version");
+    if (opt.sigma_t_mode < 0 || opt.sigma_t_mode > 2)
+        return fail(CP_EINVAL, "cp_plan: sigma_t_mode must be 0, 1 or 2");
+    if (opt.sigma_t_mode == CP_SIGMA_T_FIXED && !(opt.sigma_t > 0.f && std::isfinite(opt.sigma_t)))
+        return fail(CP_EINVAL, "cp_plan: sigma_t must be finite and > 0");
+    if (opt.sigma_t_mode == CP_SIGMA_T_PER_CURVE && !opt.sigma_t_per_curve)
+        return fail(CP_EINVAL, "cp_plan: sigma_t_per_curve is NULL");
+    if (!(opt.alpha > 0.f && std::isfinite(opt.alpha)))
+        return fail(CP_EINVAL, "cp_plan: alpha must be finite and > 0");
+    if (opt.input_memory != CP_MEM_HOST && opt.input_memory != CP_MEM_DEVICE)
+        return fail(CP_EINVAL, "cp_plan: input_memory must be CP_MEM_HOST or CP_MEM_DEVICE");
+    const cp_freq_grid g = *grid;
+    if (!(std::isfinite(g.f_min) && g.f_min >= 0.0 && std::isfinite(g.df) && g.df > 0.0))
+        return fail(CP_EINVAL, "cp_plan: need finite f_min >= 0 and df > 0");
+    if (g.n_freq < 1 || g.n_freq > ((int64_t)1 << 31) - 1)
+        return fail(CP_EINVAL, "cp_plan: n_freq must be in [1, 2^31)");
+    p->f_max = g.f_min + (double)(g.n_freq - 1) * g.df;
+    if (g.hierarchical) {
+        if (!(g.coarse_df > 0.0 && std::isfinite(g.coarse_df) && g.fine_df > 0.0 && std::isfinite(g.fine_df) &&
+              g.fine_halfwidth >= 0.0 && std::isfinite(g.fine_halfwidth)))
+            return fail(CP_EINVAL, "cp_plan: hierarchical grid needs coarse_df > 0, fine_df > 0, fine_halfwidth >= 0");
+        if (g.top_k < 1 || g.top_k > 1024)
+            return fail(CP_EINVAL, "cp_plan: top_k must be in [1, 1024]");
+        p->kc = (int64_t)std::floor((p->f_max - g.f_min) / g.coarse_df + 0.5) + 1;
+        const double jd = std::floor(g.fine_halfwidth / g.fine_df + 0.5);
+        if (jd > 1e6 || (2.0 * jd + 1.0) * g.top_k > 2e9 || p->kc > ((int64_t)1 << 31) - 1)
+            return fail(CP_EINVAL, "cp_plan: hierarchical grid too large");
+        p->J = (int)jd;
+    }
+
+    // curve sizes
+    if (offsets[0] != 0) return fail(CP_EINVAL, "cp_plan: offsets[0] must be 0");
+    p->offsets.assign(offsets, offsets + n_curves + 1);
+    p->n_curves = n_curves;
+    p->fc.resize(n_curves);
+    int max_n = 0;
+    for (int64_t c = 0; c < n_curves; c++) {
+        const int64_t n = offsets[c + 1] - offsets[c];
+        if (n < 2) return fail(CP_EINVAL, "cp_plan: curve " + std::to_string(c) + " has fewer than 2 samples");
+        if (n > kMaxN)
+            return fail(CP_EUNSUPPORTED, "cp_plan: curve " + std::to_string(c) + " has " + std::to_string(n) +
+                                             " samples; the maximum is " + std::to_string(kMaxN));
+        max_n = std::max(max_n, (int)n);
+        p->fc[c] = fc_for((int)n);
+    }
+    p->n_points = offsets[n_curves];
+    p->max_n = max_n;
+    while (p->np2max < max_n) p->np2max <<= 1;
+    p->grid = g;
+    p->opt = opt;
+    p->times = times;
+    p->mags = mags;
+    p->errs = errs;
+    p->host_inputs = opt.input_memory == CP_MEM_HOST;
+
+    // device, stream
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
+        return fail(CP_ECUDA, "cp_plan: no CUDA device available");
+    if (opt.device < 0 || opt.device >= ndev) return fail(CP_EINVAL, "cp_plan: bad device ordinal");
+    p->device = opt.device;
+    CP_CUDA(cudaSetDevice(p->device));
+    CP_CUDA(cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device));
+    p->stream = (cudaStream_t)stream;
+    CP_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+
+    // pointer kinds
+    auto kind = [](const void* ptr) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return cudaMemoryTypeUnregistered;
+        }
+        return at.type;
+    };
+    if (p->host_inputs) {
+        const bool pt = kind(times) == cudaMemoryTypeHost, pm = kind(mags) == cudaMemoryTypeHost,
+                   pe = kind(errs) == cudaMemoryTypeHost;
+        p->host_pinned = pt && pm && pe;
+    } else {
+        for (const void* q : {(const void*)times, (const void*)mags, (const void*)errs}) {
+            const cudaMemoryType k = kind(q);
+            if (k != cudaMemoryTypeDevice && k != cudaMemoryTypeManaged)
+                return fail(CP_EINVAL, "cp_plan: input_memory is CP_MEM_DEVICE but an input is not device memory");
+        }
+    }
+
+    // schedule: slots sorted by N descending (stable)
+    p->order.resize(n_curves);
+    std::iota(p->order.begin(), p->order.end(), 0);
+    std::stable_sort(p->order.begin(), p->order.end(), [&](int32_t a, int32_t b) {
+        return (offsets[a + 1] - offsets[a]) > (offsets[b + 1] - offsets[b]);
+    });
+    p->unit_full.assign(n_curves + 1, 0);
+    p->unit_coarse.assign(n_curves + 1, 0);
+    p->unit_fine.assign(n_curves + 1, 0);
+    p->wtile.assign(n_curves + 1, 0);
+    double pf_full = 0, pf_search = 0;
+    size_t smem = 0;
+    for (int64_t s = 0; s < n_curves; s++) {
+        const int c = p->order[s];
+        const int n = (int)(offsets[c + 1] - offsets[c]);
+        const int f = p->fc[c];
+        const double pairs = 0.5 * (double)n * (double)(n - 1);
+        p->unit_full[s + 1] = p->unit_full[s] + (g.n_freq + f - 1) / f;
+        if (g.hierarchical) {
+            p->unit_coarse[s + 1] = p->unit_coarse[s] + (p->kc + f - 1) / f;
+            p->unit_fine[s + 1] = p->unit_fine[s] + (int64_t)g.top_k * ((2 * p->J + 1 + f - 1) / f);
+            pf_search += pairs * (double)(p->kc + (int64_t)g.top_k * (2 * p->J + 1));
+        } else {
+            pf_search += pairs * (double)g.n_freq;
+        }
+        pf_full += pairs * (double)g.n_freq;
+        p->wtile[s + 1] = p->wtile[s] + tiles_of(n);
+        const size_t npad = (size_t)((n + kTile - 1) / kTile * kTile);
+        smem = std::max(smem, npad * (size_t)f * 12);
+    }
+    p->pf_full = pf_full;
+    p->pf_search = pf_search;
+    p->pair_smem = smem;
+
+    // waves bounded by the W buffer budget
+    size_t free_b = 0, total_b = 0;
+    CP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 3);
+    if (const char* env = std::getenv("CP_W_BUDGET_KB")) budget = (size_t)std::atoll(env) << 10;
+    const int64_t tile_budget = std::max<int64_t>(1, (int64_t)(budget / (kTileFloats * sizeof(float))));
+    int64_t max_wave_tiles = 0;
+    {
+        int sb = 0;
+        for (int s = 0; s < (int)n_curves; s++) {
+            const int64_t t_end = p->wtile[s + 1];
+            if (t_end - p->wtile[sb] > tile_budget && s > sb) {
+                p->waves.push_back({sb, s, p->wtile[sb], p->wtile[s]});
+                max_wave_tiles = std::max(max_wave_tiles, p->wtile[s] - p->wtile[sb]);
+                sb = s;
+            }
+        }
+        p->waves.push_back({sb, (int)n_curves, p->wtile[sb], p->wtile[n_curves]});
+        max_wave_tiles = std::max(max_wave_tiles, p->wtile[n_curves] - p->wtile[sb]);
+    }
+
+    // device allocation (one block)
+    const int64_t np = p->n_points, nc = n_curves;
+    const int nq = 3 * (int)p->waves.size();
+    p->n_u64 = 1 + nc + nq;
+    struct Part { void** dst; size_t bytes; };
+    const bool hier = g.hierarchical != 0;
+    std::vector<Part> parts = {
+        {(void**)&p->d_times, p->host_inputs ? np * sizeof(double) : 0},
+        {(void**)&p->d_mags, p->host_inputs ? np * sizeof(float) : 0},
+        {(void**)&p->d_errs, p->host_inputs ? np * sizeof(float) : 0},
+        {(void**)&p->d_cp, nc * sizeof(CurveParams)},
+        {(void**)&p->d_yp, np * sizeof(float)},
+        {(void**)&p->d_ph_base, np * sizeof(uint64_t)},
+        {(void**)&p->d_ph_full, np * sizeof(uint64_t)},
+        {(void**)&p->d_ph_coarse, hier ? np * sizeof(uint64_t) : 0},
+        {(void**)&p->d_ph_fine, hier ? np * sizeof(uint64_t) : 0},
+        {(void**)&p->d_stpc, opt.sigma_t_mode == CP_SIGMA_T_PER_CURVE ? nc * sizeof(float) : 0},
+        {(void**)&p->d_order, nc * sizeof(int32_t)},
+        {(void**)&p->d_unit_full, (nc + 1) * sizeof(int64_t)},
+        {(void**)&p->d_unit_coarse, (nc + 1) * sizeof(int64_t)},
+        {(void**)&p->d_unit_fine, (nc + 1) * sizeof(int64_t)},
+        {(void**)&p->d_wtile, (nc + 1) * sizeof(int64_t)},
+        {(void**)&p->d_W, (size_t)max_wave_tiles * kTileFloats * sizeof(float)},
+        {(void**)&p->d_coarse, hier ? (size_t)nc * p->kc * sizeof(float) : 0},
+        {(void**)&p->d_peaks, hier ? (size_t)nc * g.top_k * sizeof(int32_t) : 0},
+        {(void**)&p->d_npeaks, hier ? nc * sizeof(int32_t) : 0},
+        {(void**)&p->d_u64, (size_t)p->n_u64 * sizeof(unsigned long long)},
+        {(void**)&p->d_res_idx, nc * sizeof(int64_t)},
+        {(void**)&p->d_res_freq, nc * sizeof(double)},
+        {(void**)&p->d_res_stat, nc * sizeof(float)},
+        {(void**)&p->d_res_per, nc},
+        {(void**)&p->d_res_psnr, nc * sizeof(float)},
+    };
+    size_t total = 0;
+    for (auto& q : parts) total = align_up(total, 256) + q.bytes;
+    CP_CUDA(cudaMalloc(&p->dblock, std::max<size_t>(total, 256)));
+    {
+        size_t o = 0;
+        for (auto& q : parts) {
+            o = align_up(o, 256);
+            *q.dst = q.bytes ? (void*)((char*)p->dblock + o) : nullptr;
+            o += q.bytes;
+        }
+    }
+    // pinned host block
+    std::vector<Part> hparts = {
+        {(void**)&p->h_res_idx, nc * sizeof(int64_t)},
+        {(void**)&p->h_res_freq, nc * sizeof(double)},
+        {(void**)&p->h_res_stat, nc * sizeof(float)},
+        {(void**)&p->h_res_per, (size_t)nc},
+        {(void**)&p->h_res_psnr, nc * sizeof(float)},
+        {(void**)&p->h_status, sizeof(unsigned long long)},
+        {(void**)&p->h_times, p->host_inputs && !p->host_pinned ? np * sizeof(double) : 0},
+        {(void**)&p->h_mags, p->host_inputs && !p->host_pinned ? np * sizeof(float) : 0},
+        {(void**)&p->h_errs, p->host_inputs && !p->host_pinned ? np * sizeof(float) : 0},
+    };
+    size_t htotal = 0;
+    for (auto& q : hparts) htotal = align_up(htotal, 64) + q.bytes;
+    CP_CUDA(cudaMallocHost(&p->hblock, std::max<size_t>(htotal, 64)));
+    {
+        size_t o = 0;
+        for (auto& q : hparts) {
+            o = align_up(o, 64);
+            *q.dst = q.bytes ? (void*)((char*)p->hblock + o) : nullptr;
+            o += q.bytes;
+        }
+    }
+
+    // per-curve constants and schedule tables
+    std::vector<CurveParams> cps(nc);
+    for (int64_t c = 0; c < nc; c++) {
+        std::memset(&cps[c], 0, sizeof(CurveParams));
+        cps[c].off = offsets[c];
+        cps[c].n = (int32_t)(offsets[c + 1] - offsets[c]);
+        cps[c].fc = p->fc[c];
+    }
+    CP_CUDA(cudaMemcpy(p->d_cp, cps.data(), nc * sizeof(CurveParams), cudaMemcpyHostToDevice));
+    CP_CUDA(cudaMemcpy(p->d_order, p->order.data(), nc * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CP_CUDA(cudaMemcpy(p->d_unit_full, p->unit_full.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CP_CUDA(cudaMemcpy(p->d_unit_coarse, p->unit_coarse.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CP_CUDA(cudaMemcpy(p->d_unit_fine, p->unit_fine.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CP_CUDA(cudaMemcpy(p->d_wtile, p->wtile.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (opt.sigma_t_mode == CP_SIGMA_T_PER_CURVE) {
+        for (int64_t c = 0; c < nc; c++)
+            if (!(opt.sigma_t_per_curve[c] > 0.f && std::isfinite(opt.sigma_t_per_curve[c])))
+                return fail(CP_EINVAL, "cp_plan: sigma_t_per_curve values must be finite and > 0");
+        CP_CUDA(cudaMemcpy(p->d_stpc, opt.sigma_t_per_curve, nc * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    p->opt.sigma_t_per_curve = nullptr;
+
+    // launch geometry of the persistent pair kernel
+    CP_CUDA(prepare_kernels(p->np2max, p->pair_smem));
+    int occ = 1;
+    CP_CUDA(pair_direct_occupancy(&occ, p->pair_smem));
+    p->pair_grid = p->n_sm * std::max(occ, 1);
+
+    // events
+    const int pair_launches = (int)p->waves.size() * (g.hierarchical ? 2 : 1);
+    p->ev_pair.resize(2 * pair_launches);
+    for (auto& e : p->ev_pair) CP_CUDA(cudaEventCreate(&e));
+    CP_CUDA(cudaEventCreate(&p->ev_step0));
+    CP_CUDA(cudaEventCreate(&p->ev_step1));
+    p->launches_per_search =
+        2 /* zero, stats */ + (int64_t)p->waves.size() * (g.hierarchical ? 4 : 2) + 1 /* finalize */;
+    return CP_OK;
+}
+
+cp_status cp_plan(const double* times, const float* mags, const float* errs, const int64_t* offsets,
+                  int64_t n_curves, const cp_freq_grid* grid, const cp_options* opt, void* stream,
+                  cp_plan_t* out_plan)
+{
+    if (!out_plan) return fail(CP_EINVAL, "cp_plan: out_plan is NULL");
+    *out_plan = nullptr;
+    cp_plan_s* p = new (std::nothrow) cp_plan_s();
+    if (!p) return fail(CP_ENOMEM, "cp_plan: host allocation failed");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cp_status st = plan_impl(times, mags, errs, offsets, n_curves, grid, opt, stream, p);
+    cudaSetDevice(prev);
+    if (st != CP_OK) {
+        std::string msg = g_last_error;
+        cp_destroy(p);
+        g_last_error = msg;
+        return st;
+    }
+    *out_plan = p;
+    return finish(CP_OK, "cp_plan");
+}
+
+static cp_status periodogram_impl(cp_plan_t p, float* out)
+{
+    if (!p) return fail(CP_EINVAL, "cp_periodogram: NULL plan");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    CP_CUDA(cudaSetDevice(p->device));
+    cp_status st = CP_OK;
+    // the pinned staging copy must not overwrite data a previous call still reads
+    if (p->host_inputs && !p->host_pinned) CP_CUDA(cudaStreamSynchronize(p->stream));
+    stage_host_inputs(p);
+    if ((st = enqueue_inputs(p, p->stream)) == CP_OK && (st = enqueue_stats(p, p->stream)) == CP_OK) {
+        for (int w = 0; w < (int)p->waves.size() && st == CP_OK; w++) {
+            st = enqueue_wave_w(p, w, p->stream);
+            if (st == CP_OK) st = enqueue_pair(p, kStageFull, w, out, p->stream, nullptr);
+        }
+    }
+    if (st == CP_OK)
+        CP_CUDA(cudaMemcpyAsync(p->h_status, p->d_u64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->stream));
+    p->ran = true;
+    cudaSetDevice(prev);
+    return st;
+}
+
+static cp_status sync_impl(cp_plan_t p)
+{
+    if (!p) return fail(CP_EINVAL, "cp_sync: NULL plan");
+    CP_CUDA(cudaSetDevice(p->device));
+    CP_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->ran && *p->h_status)
+        return fail(CP_EINVAL, "input contains a non-finite value, a zero median error bar or a bad sigma_t");
+    return CP_OK;
+}
+
+static cp_status best_period_impl(cp_plan_t p, int64_t* best_idx, double* best_freq, float* best_stat,
+                                  uint8_t* is_periodic, float* psnr)
+{
+    if (!p) return fail(CP_EINVAL, "cp_best_period: NULL plan");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    CP_CUDA(cudaSetDevice(p->device));
+    cp_status st = CP_OK;
+    // the pinned staging copy must not overwrite data a previous call still reads
+    if (p->host_inputs && !p->host_pinned) CP_CUDA(cudaStreamSynchronize(p->stream));
+    stage_host_inputs(p);
+    if (p->opt.use_graph) {
+        if (!p->graph_ready) st = build_graph(p);
+        if (st == CP_OK) CP_CUDA(cudaGraphLaunch(p->exec, p->stream));
+    } else {
+        st = enqueue_search(p, p->stream);
+    }
+    if (st != CP_OK) {
+        cudaSetDevice(prev);
+        return st;
+    }
+    CP_CUDA(cudaStreamSynchronize(p->stream));
+    p->ran = true;
+    if ((st = read_timings(p)) != CP_OK) {
+        cudaSetDevice(prev);
+        return st;
+    }
+    const size_t nc = (size_t)p->n_curves;
+    if (best_idx) std::memcpy(best_idx, p->h_res_idx, nc * sizeof(int64_t));
+    if (best_freq) std::memcpy(best_freq, p->h_res_freq, nc * sizeof(double));
+    if (best_stat) std::memcpy(best_stat, p->h_res_stat, nc * sizeof(float));
+    if (is_periodic) std::memcpy(is_periodic, p->h_res_per, nc);
+    if (psnr) std::memcpy(psnr, p->h_res_psnr, nc * sizeof(float));
+    cudaSetDevice(prev);
+    if (*p->h_status)
+        return fail(CP_EINVAL, "input contains a non-finite value, a zero median error bar or a bad sigma_t");
+    return CP_OK;
+}
+
+static cp_status curve_stats_impl(cp_plan_t p, float* sigma_y, float* sigma_t, double* ip, float* psnr)
+{
+    if (!p) return fail(CP_EINVAL, "cp_curve_stats: NULL plan");
+    if (!p->ran) return fail(CP_ESTATE, "cp_curve_stats: no call has run on this plan yet");
+    CP_CUDA(cudaSetDevice(p->device));
+    CP_CUDA(cudaStreamSynchronize(p->stream));
+    std::vector<CurveParams> cps((size_t)p->n_curves);
+    CP_CUDA(cudaMemcpy(cps.data(), p->d_cp, cps.size() * sizeof(CurveParams), cudaMemcpyDeviceToHost));
+    for (size_t c = 0; c < cps.size(); c++) {
+        if (sigma_y) sigma_y[c] = cps[c].sigma_y;
+        if (sigma_t) sigma_t[c] = cps[c].sigma_t;
+        if (ip) ip[c] = cps[c].ip / (std::sqrt(2.0 * M_PI) * (double)cps[c].sigma_y);
+        if (psnr) psnr[c] = cps[c].psnr;
+    }
+    return CP_OK;
+}
+
+cp_status cp_periodogram(cp_plan_t p, float* out) { return finish(periodogram_impl(p, out), "cp_periodogram"); }
+
+cp_status cp_sync(cp_plan_t p) { return finish(sync_impl(p), "cp_sync"); }
+
+cp_status cp_best_period(cp_plan_t p, int64_t* best_idx, double* best_freq, float* best_stat,
+                         uint8_t* is_periodic, float* psnr)
+{
+    return finish(best_period_impl(p, best_idx, best_freq, best_stat, is_periodic, psnr), "cp_best_period");
+}
+
+cp_status cp_curve_stats(cp_plan_t p, float* sigma_y, float* sigma_t, double* ip, float* psnr)
+{
+    return finish(curve_stats_impl(p, sigma_y, sigma_t, ip, psnr), "cp_curve_stats");
+}
+
+cp_status cp_get_plan_info(cp_plan_t p, cp_plan_info* info)
+{
+    if (!p || !info) return fail(CP_EINVAL, "cp_get_plan_info: NULL argument");
+    info->n_curves = p->n_curves;
+    info->n_points = p->n_points;
+    info->pair_freq_full = p->pf_full;
+    info->pair_freq_search = p->pf_search;
+    info->launches_per_search = p->launches_per_search;
+    info->last_pair_kernel_ms = p->last_pair_ms;
+    info->last_step_ms = p->last_step_ms;
+    info->n_sm = p->n_sm;
+    info->max_n = p->max_n;
+    return CP_OK;
+}
+
+cp_status cp_bessel_coefficients(double sigma_t, int32_t n_max, double* out)
+{
+    if (!out || n_max < 0 || n_max > 100000 || !(sigma_t > 0.0) || !std::isfinite(sigma_t))
+        return fail(CP_EINVAL, "cp_bessel_coefficients: bad argument");
+    const double kappa = 1.0 / (sigma_t * sigma_t);
+    // trapezoid rule on [0, pi] for the even periodic integrand (exponentially convergent)
+    const int M = std::max(2048, 8 * (int)(kappa + n_max) + 64);
+    for (int n = 0; n <= n_max; n++) {
+        double acc = 0.0;
+        for (int k = 0; k <= M; k++) {
+            const double th = M_PI * (double)k / (double)M;
+            const double wgt = (k == 0 || k == M) ? 0.5 : 1.0;
+            acc += wgt * std::exp(kappa * (std::cos(th) - 1.0)) * std::cos((double)n * th);
+        }
+        acc /= (double)M;                 // (1/pi) * (pi/M) * sum
+        out[n] = (n == 0) ? acc : 2.0 * acc;
+    }
+    return CP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,587 @@
+// cp_kernels.cu -- sm_103a kernels of the correntropy kernelized periodogram.
+//
+// Hot path (arXiv:1412.1840, Section 3, Eq. (HP), (IP), (CKP)):
+//   k_stats        per-curve scalars (sigma_y = med(e), pSNR, sigma_t, IP),
+//                  scaled magnitudes y' and 64-bit fixed-point phase steps
+//   k_build_w      period-independent magnitude-kernel tiles w_ij = g_ij - ip
+//   k_pair_direct  persistent pair-sum kernel over (curve, frequency-chunk)
+//                  work units: the N(N-1)/2 interactions of Section 7 per
+//                  trial frequency, FP32 with packed f32x2 arithmetic
+//   k_topk         coarse-grid local maxima for the coarse-then-fine search
+//   k_finalize     best frequency, nCKP and Table tab:th discriminator
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cp_internal.cuh"
+
+namespace cpk {
+
+// Table "tab:th" of Section 4.1: pSNR bin lower edges and thresholds.
+__constant__ double c_bin_lo[8] = {0.0, 1.5, 2.0, 2.5, 3.5, 5.0, 10.0, 20.0};
+__constant__ float c_th[8] = {0.4584f, 0.4565f, 0.4537f, 0.4581f, 0.5875f, 1.1153f, 1.6464f, 2.4112f};
+
+// ===========================================================================
+// k_stats: one CTA per curve.
+// ===========================================================================
+
+constexpr int kStatsThreads = 256;
+
+__device__ __forceinline__ double median_sorted(const float* s, int n)
+{
+    return (n & 1) ? (double)s[n >> 1] : 0.5 * ((double)s[(n >> 1) - 1] + (double)s[n >> 1]);
+}
+
+// Quantile by linear interpolation between order statistics at q*(n-1).
+__device__ __forceinline__ double quantile_sorted(const float* s, int n, double q)
+{
+    const double pos = q * (double)(n - 1);
+    const int lo = (int)floor(pos);
+    const int hi = lo + 1 < n ? lo + 1 : n - 1;
+    return (double)s[lo] + (pos - (double)lo) * ((double)s[hi] - (double)s[lo]);
+}
+
+__device__ __forceinline__ int snr_bin(double p)
+{
+    int b = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+        if (p >= c_bin_lo[k]) b = k;
+    return b;
+}
+
+__global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* ts = reinterpret_cast<double*>(smem);
+    float* ys = reinterpret_cast<float*>(ts + a.np2max);
+    float* es = ys + a.np2max;
+    float* ypl = es + a.np2max;
+    __shared__ double s_red[kStatsThreads / 32];
+    __shared__ double s_t0;
+    __shared__ float s_yref, s_gamma;
+    __shared__ int s_bad;
+
+    const int c = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    CurveParams* P = a.cp + c;
+    const int64_t off = P->off;
+    const int n = P->n;
+    int np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+
+    // 1. load, validate, min t
+    double tmin = INFINITY;
+    for (int i = tid; i < np2; i += kStatsThreads) {
+        if (i < n) {
+            const double t = a.times[off + i];
+            const float y = a.mags[off + i];
+            const float e = a.errs[off + i];
+            if (!isfinite(t) || !isfinite(y) || !isfinite(e)) s_bad = 1;
+            ts[i] = t;
+            ys[i] = y;
+            es[i] = e;
+            tmin = fmin(tmin, t);
+        } else {
+            ys[i] = INFINITY;
+            es[i] = INFINITY;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+    if (lane == 0) s_red[warp] = tmin;
+    __syncthreads();
+    if (tid == 0) {
+        double m = s_red[0];
+        for (int w = 1; w < kStatsThreads / 32; w++) m = fmin(m, s_red[w]);
+        s_t0 = m;
+    }
+
+    // 2. bitonic sort of magnitudes and error bars (ascending)
+    for (int k = 2; k <= np2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            __syncthreads();
+            for (int i = tid; i < np2; i += kStatsThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    float u = ys[i], v = ys[ixj];
+                    if ((u > v) == up) { ys[i] = v; ys[ixj] = u; }
+                    u = es[i]; v = es[ixj];
+                    if ((u > v) == up) { es[i] = v; es[ixj] = u; }
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // 3. per-curve scalars (FP64, one thread)
+    if (tid == 0) {
+        const double sy = median_sorted(es, n);
+        const double yref = median_sorted(ys, n);
+        const double q1 = quantile_sorted(ys, n, 0.25), q3 = quantile_sorted(ys, n, 0.75);
+        const double psnr = 0.7413 * (q3 - q1) / ((double)a.alpha * sy);
+        double st;
+        if (a.sigma_t_mode == 1) {
+            st = (double)a.sigma_t_per_curve[c];
+        } else if (a.sigma_t_mode == 2) {
+            // Bowley skewness, quartiles = medians of the lower / upper halves
+            const int h = n >> 1;
+            const double lq = median_sorted(ys, h), uq = median_sorted(ys + (n - h), h);
+            const double sk = (uq == lq) ? 0.0 : (uq + lq - 2.0 * yref) / (uq - lq);
+            st = 0.1 + 0.5 * exp(-12.0 * sk * sk);
+        } else {
+            st = (double)a.sigma_t;
+        }
+        if (!(sy > 0.0) || !isfinite(sy) || !(st > 0.0) || !isfinite(st)) s_bad = 1;
+        const float stf = (float)st;
+        P->sigma_y = (float)sy;
+        P->sigma_t = stf;
+        P->psnr = (float)psnr;
+        P->th = c_th[snr_bin(psnr)];
+        P->t0 = s_t0;
+        const double gamma = sqrt(1.4426950408889634 / (2.0 * sy * sy));
+        s_yref = (float)yref;
+        s_gamma = (float)gamma;
+        P->gamma = (float)gamma;
+        // sqrt(beta), beta = sqrt(2 log2 e) / sigma_t
+        P->tscale = (float)sqrt(sqrt(2.0 * 1.4426950408889634) / (double)stf);
+    }
+    __syncthreads();
+
+    // 4. scaled magnitudes y' = (y - y_ref) * gamma (same values feed IP and W)
+    const float yref = s_yref, gamma = s_gamma;
+    for (int i = tid; i < n; i += kStatsThreads) {
+        const float v = (a.mags[off + i] - yref) * gamma;
+        ypl[i] = v;
+        a.yp[off + i] = v;
+    }
+    __syncthreads();
+
+    // 5. IP: ip = (N + 2 sum_{i<j} g_ij) / N^2, FP64 accumulation
+    double acc = 0.0;
+    for (int i = tid; i < n; i += kStatsThreads) {
+        const float yi = ypl[i];
+        for (int j = i + 1; j < n; j++) acc += (double)gauss_g(yi, ypl[j]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __syncthreads();
+    if (lane == 0) s_red[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double s2 = 0.0;
+        for (int w = 0; w < kStatsThreads / 32; w++) s2 += s_red[w];
+        const double nn = (double)n;
+        const double ip = (nn + 2.0 * s2) / (nn * nn);
+        const float iph = (float)ip;
+        P->ip = ip;
+        P->ip_hi = iph;
+        P->ip_lo = (float)(ip - (double)iph);
+        P->norm = (float)(sqrt(nn) / (nn * nn * ip * sqrt(2.0 * CP_PI) * sqrt((double)P->sigma_t)));
+        P->diag = (float)(nn * (1.0 - ip));
+        if (s_bad) atomicOr(a.status, 1);
+    }
+
+    // 6. fixed-point phase steps of t - t0 for each grid the search uses
+    const double t0 = s_t0;
+    for (int i = tid; i < n; i += kStatsThreads) {
+        const double tp = ts[i] - t0;
+        a.ph_base[off + i] = fixfrac(a.f_min, tp);
+        a.ph_full[off + i] = fixfrac(a.df, tp);
+        if (a.hierarchical) {
+            a.ph_coarse[off + i] = fixfrac(a.coarse_df, tp);
+            a.ph_fine[off + i] = fixfrac(a.fine_df, tp);
+        }
+    }
+}
+
+// ===========================================================================
+// k_build_w: one warp per 32x32 tile of the upper block triangle.
+// Layout per tile: [k][lane][m] floats, k < 8 rows, m < 4 columns per lane.
+// ===========================================================================
+
+__device__ __forceinline__ void decode_tile(int t, int nb, int& bi, int& bj)
+{
+    int b = 0, rem = t;
+    while (rem >= nb - b) { rem -= nb - b; ++b; }
+    bi = b;
+    bj = b + rem;
+}
+
+__global__ void __launch_bounds__(256) k_build_w(const BuildWArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t T = a.tile_begin + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (T >= a.tile_end) return;
+    int lo = a.slot_begin, hi = a.slot_end - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.wtile_start[mid] <= T) lo = mid; else hi = mid - 1;
+    }
+    const int c = a.order[lo];
+    const CurveParams P = a.cp[c];
+    const int n = P.n;
+    const int nb = (n + kTile - 1) / kTile;
+    int bi, bj;
+    decode_tile((int)(T - a.wtile_start[lo]), nb, bi, bj);
+    const int la = lane >> 3, lb = lane & 7;
+    float ypc[kColsPerLane];
+    int jj[kColsPerLane];
+#pragma unroll
+    for (int m = 0; m < kColsPerLane; m++) {
+        jj[m] = bj * kTile + lb + 8 * m;
+        ypc[m] = jj[m] < n ? a.yp[P.off + jj[m]] : 0.f;
+    }
+    float* dst = a.W + (T - a.tile_begin) * kTileFloats;
+#pragma unroll
+    for (int k = 0; k < kRowsPerLane; k++) {
+        const int i = bi * kTile + la + 4 * k;
+        const float ypr = i < n ? a.yp[P.off + i] : 0.f;
+        float w[kColsPerLane];
+#pragma unroll
+        for (int m = 0; m < kColsPerLane; m++) {
+            const float g = gauss_g(ypr, ypc[m]);
+            w[m] = (i < jj[m] && jj[m] < n) ? (g - P.ip_hi) - P.ip_lo : 0.f;
+        }
+        reinterpret_cast<float4*>(dst)[k * 32 + lane] = make_float4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// ===========================================================================
+// k_pair_direct: persistent CTAs pop (curve, frequency-chunk) units.
+// ===========================================================================
+constexpr int kPairThreads = 256;
+
+__global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs a)
+{
+    constexpr int NW = kPairThreads / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_unit;
+    __shared__ float s_red[NW][kFcMax];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int la = lane >> 3, lb = lane & 7;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_unit = (long long)atomicAdd(a.queue, 1ull) + a.unit_begin;
+        __syncthreads();
+        const long long u = s_unit;
+        if (u >= a.unit_end) break;
+
+        int lo = a.slot_begin, hi = a.slot_end - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.unit_start[mid] <= u) lo = mid; else hi = mid - 1;
+        }
+        const int slot = lo;
+        const int c = a.order[slot];
+        const CurveParams& P = a.cp[c];
+        const int n = P.n, fc = P.fc, nfp = fc >> 1;
+        const int npad = (n + kTile - 1) & ~(kTile - 1);
+        const long long chunk = u - a.unit_start[slot];
+        const int64_t off = P.off;
+
+        // frequencies of this unit: phase(i, kk) = base_i + mult0 * step_i + kk * step_i
+        long long kfirst;      // full/coarse: first grid index; fine: first j
+        int count;
+        int peak = 0;
+        uint64_t peak_mult = 0;  // fine: coarse peak index (phase offset kpeak * coarse_i)
+        if (a.stage == kStageFine) {
+            const int W = 2 * a.fine_half + 1;
+            const int upp = (W + fc - 1) / fc;
+            peak = (int)(chunk / upp);
+            const int sub = (int)(chunk - (long long)peak * upp);
+            if (peak >= a.n_peaks[c]) continue;
+            peak_mult = (uint64_t)a.peaks[(int64_t)c * a.top_k + peak];
+            kfirst = -a.fine_half + (long long)sub * fc;
+            count = (int)min((long long)fc, (long long)a.fine_half - kfirst + 1);
+        } else {
+            kfirst = chunk * fc;
+            count = (int)min((long long)fc, a.n_freq - kfirst);
+        }
+
+        // trig table: SC[fp][i] = {(s_f, s_f'), (c_f, c_f')} * sqrt(beta), NS[fp][i] = -(s_f, s_f')
+        ulonglong2* SC = reinterpret_cast<ulonglong2*>(smem);
+        f2* NS = reinterpret_cast<f2*>(SC + nfp * npad);
+        const float ts = P.tscale;
+        for (int it = tid; it < nfp * npad; it += kPairThreads) {
+            const int fp = it / npad, i = it - fp * npad;
+            ulonglong2 v = make_ulonglong2(0ull, 0ull);
+            f2 ns = 0ull;
+            if (i < n) {
+                const uint64_t st = a.ph_step[off + i];
+                uint64_t ph = a.ph_base[off + i] + (uint64_t)(kfirst + 2 * fp) * st;
+                if (a.stage == kStageFine) ph += peak_mult * a.ph_coarse[off + i];
+                float s0, c0, s1, c1;
+                sincospi_turns((uint32_t)(ph >> 32), s0, c0);
+                sincospi_turns((uint32_t)((ph + st) >> 32), s1, c1);
+                s0 *= ts; c0 *= ts; s1 *= ts; c1 *= ts;
+                v = make_ulonglong2(pk(s0, s1), pk(c0, c1));
+                ns = pk(-s0, -s1);
+            }
+            SC[it] = v;
+            NS[it] = ns;
+        }
+        __syncthreads();
+
+        const int nb = npad / kTile;
+        const int ntiles = nb * (nb + 1) / 2;
+        const float* Wc = a.W + (a.wtile_start[slot] - a.wtile_base) * kTileFloats;
+        f2 accF[kFcMax / 2], accG[kFcMax / 2];   // per f-pair: frequency f (accF) and f' (accG)
+#pragma unroll
+        for (int q = 0; q < kFcMax / 2; q++) { accF[q] = 0ull; accG[q] = 0ull; }
+
+        for (int t = warp; t < ntiles; t += NW) {
+            int bi, bj;
+            decode_tile(t, nb, bi, bj);
+            const float4* Wt = reinterpret_cast<const float4*>(Wc + (int64_t)t * kTileFloats);
+            f2 w01[kRowsPerLane], w23[kRowsPerLane];
+#pragma unroll
+            for (int k = 0; k < kRowsPerLane; k++) {
+                const float4 v = __ldg(Wt + k * 32 + lane);
+                w01[k] = pk(v.x, v.y);
+                w23[k] = pk(v.z, v.w);
+            }
+            const int rbase = bi * kTile + la;
+            const int cbase = bj * kTile + lb;
+#pragma unroll
+            for (int fp = 0; fp < kFcMax / 2; fp++) {
+                if (fp < nfp) {
+                    const ulonglong2* SCf = SC + fp * npad;
+                    const f2* NSf = NS + fp * npad;
+                    ulonglong2 col[kColsPerLane];
+#pragma unroll
+                    for (int m = 0; m < kColsPerLane; m++) col[m] = SCf[cbase + 8 * m];
+                    f2 tf0 = 0ull, tf1 = 0ull, tg0 = 0ull, tg1 = 0ull;
+#pragma unroll
+                    for (int k = 0; k < kRowsPerLane; k++) {
+                        const int i = rbase + 4 * k;
+                        const f2 A = SCf[i].y;   // (c_i(f), c_i(f'))
+                        const f2 B = NSf[i];     // (-s_i(f), -s_i(f'))
+                        float e[kColsPerLane][2];
+#pragma unroll
+                        for (int m = 0; m < kColsPerLane; m++) {
+                            const f2 t2 = mul2(B, col[m].y);
+                            const f2 d2 = fma2(A, col[m].x, t2);
+                            const f2 q2 = mul2(d2, d2);
+                            float q0, q1;
+                            upk(q2, q0, q1);
+                            e[m][0] = ex2_approx(-q0);
+                            e[m][1] = ex2_approx(-q1);
+                        }
+                        tf0 = fma2(w01[k], pk(e[0][0], e[1][0]), tf0);
+                        tf1 = fma2(w23[k], pk(e[2][0], e[3][0]), tf1);
+                        tg0 = fma2(w01[k], pk(e[0][1], e[1][1]), tg0);
+                        tg1 = fma2(w23[k], pk(e[2][1], e[3][1]), tg1);
+                    }
+                    accF[fp] = add2(accF[fp], add2(tf0, tf1));
+                    accG[fp] = add2(accG[fp], add2(tg0, tg1));
+                }
+            }
+        }
+
+        // warp reduction of the 2*nfp frequency sums, then a fixed-order CTA sum
+#pragma unroll
+        for (int fp = 0; fp < kFcMax / 2; fp++) {
+            if (fp < nfp) {
+                float a0, a1, b0, b1;
+                upk(accF[fp], a0, a1);
+                upk(accG[fp], b0, b1);
+                float vf = a0 + a1, vg = b0 + b1;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    vf += __shfl_xor_sync(0xffffffffu, vf, o);
+                    vg += __shfl_xor_sync(0xffffffffu, vg, o);
+                }
+                if (lane == 0) {
+                    s_red[warp][2 * fp] = vf;
+                    s_red[warp][2 * fp + 1] = vg;
+                }
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long key = 0ull;
+            if (lane < count) {
+                float S = 0.f;
+#pragma unroll
+                for (int w = 0; w < NW; w++) S += s_red[w][lane];
+                const float v = (2.0f * S + P.diag) * P.norm;
+                const long long kk = kfirst + lane;
+                if (a.stage == kStageFull) {
+                    if (a.out) a.out[(int64_t)c * a.out_ld + kk] = v;
+                    key = make_key(v, (uint32_t)kk);
+                } else if (a.stage == kStageCoarse) {
+                    a.coarse_out[(int64_t)c * a.n_freq + kk] = v;
+                } else {
+                    const double fpk = a.f_min + (double)peak_mult * a.coarse_df;
+                    const double f = fpk + (double)kk * a.step;
+                    if (f >= a.f_min && f <= a.f_max)
+                        key = make_key(v, (uint32_t)(peak * (2 * a.fine_half + 1) + (kk + a.fine_half)));
+                }
+            }
+            if (a.stage != kStageCoarse) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+                    key = other > key ? other : key;
+                }
+                if (lane == 0 && key) atomicMax(a.best_key + c, key);
+            }
+        }
+    }
+}
+
+// ===========================================================================
+// k_topk: one warp per curve, top_k local maxima of the coarse periodogram.
+// Local maximum: v[k] > v[k-1] and v[k] >= v[k+1]; ends use one neighbour.
+// Order: value descending, ties to the lower k (larger key).
+// ===========================================================================
+
+__global__ void __launch_bounds__(256) k_topk(const TopkArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int slot = a.slot_begin + blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (slot >= a.slot_end) return;
+    const int c = a.order[slot];
+    const float* v = a.coarse + (int64_t)c * a.n_freq;
+    const int64_t K = a.n_freq;
+    unsigned long long prev = ~0ull;
+    int cnt = 0;
+    for (int r = 0; r < a.top_k; r++) {
+        unsigned long long best = 0ull;
+        for (int64_t k = lane; k < K; k += 32) {
+            const float x = v[k];
+            const bool lok = (k == 0) || (x > v[k - 1]);
+            const bool rok = (k == K - 1) || (x >= v[k + 1]);
+            if (lok && rok) {
+                const unsigned long long key = make_key(x, (uint32_t)k);
+                if (key < prev && key > best) best = key;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other > best ? other : best;
+        }
+        if (best == 0ull) break;
+        if (lane == 0) a.peaks[(int64_t)c * a.top_k + r] = (int32_t)(0xffffffffu - (uint32_t)(best & 0xffffffffu));
+        prev = best;
+        cnt++;
+    }
+    if (lane == 0) a.n_peaks[c] = cnt;
+}
+
+// ===========================================================================
+// k_finalize: decode the best keys, apply the discriminator.
+// ===========================================================================
+
+__global__ void k_finalize(const FinalArgs a)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.n_curves) return;
+    const unsigned long long key = a.best_key[c];
+    if (key == 0ull) {   // no admissible candidate (cannot happen for valid grids)
+        a.best_idx[c] = -1;
+        a.best_freq[c] = __longlong_as_double(0x7ff8000000000000ll);
+        a.best_stat[c] = __int_as_float(0x7fc00000);
+        a.is_periodic[c] = 0;
+        a.psnr[c] = a.cp[c].psnr;
+        return;
+    }
+    const float v = from_orderable((uint32_t)(key >> 32));
+    const uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
+    double f;
+    if (a.hierarchical) {
+        const int W = 2 * a.fine_half + 1;
+        const int p = (int)(idx / (uint32_t)W);
+        const int j = (int)(idx % (uint32_t)W) - a.fine_half;
+        const double fpk = a.f_min + (double)a.peaks[(int64_t)c * a.top_k + p] * a.coarse_df;
+        f = fpk + (double)j * a.fine_df;
+    } else {
+        f = a.f_min + (double)idx * a.df;
+    }
+    a.best_idx[c] = (int64_t)idx;
+    a.best_freq[c] = f;
+    a.best_stat[c] = v;
+    a.is_periodic[c] = v > a.cp[c].th ? 1 : 0;
+    a.psnr[c] = a.cp[c].psnr;
+}
+
+__global__ void k_zero_u64(unsigned long long* p, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0ull;
+}
+
+}  // namespace cpk
+
+// ---------------------------------------------------------------------------
+// Launchers used by the host API (C++ linkage, internal to the library).
+// ---------------------------------------------------------------------------
+namespace cpk {
+
+cudaError_t launch_stats(const StatsArgs& a, int n_curves, cudaStream_t s)
+{
+    const size_t smem = stats_smem_bytes(a.np2max);
+    k_stats<<<n_curves, kStatsThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_w(const BuildWArgs& a, cudaStream_t s)
+{
+    const int64_t tiles = a.tile_end - a.tile_begin;
+    if (tiles <= 0) return cudaSuccess;
+    k_build_w<<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_direct(const PairArgs& a, int grid, size_t smem, cudaStream_t s)
+{
+    k_pair_direct<<<grid, kPairThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_topk(const TopkArgs& a, cudaStream_t s)
+{
+    const int n = a.slot_end - a.slot_begin;
+    if (n <= 0) return cudaSuccess;
+    k_topk<<<(n + 7) / 8, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const FinalArgs& a, cudaStream_t s)
+{
+    k_finalize<<<(a.n_curves + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int pair_direct_threads() { return kPairThreads; }
+
+size_t stats_smem_bytes(int np2max) { return (size_t)np2max * (sizeof(double) + 3 * sizeof(float)); }
+
+cudaError_t prepare_kernels(int np2max, size_t pair_smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_stats, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)stats_smem_bytes(np2max));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_pair_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem);
+}
+
+cudaError_t pair_direct_occupancy(int* blocks_per_sm, size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_pair_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pair_direct, kPairThreads, smem);
+}
+
+cudaError_t launch_zero_u64(unsigned long long* p, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_zero_u64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n);
+    return cudaGetLastError();
+}
+
+}  // namespace cpk

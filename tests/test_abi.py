@@ -1,0 +1,89 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/cp.h declares, validates arguments before touching a device, and its
+host-side Bessel coefficients match the paper's series (Eq. (taylor))."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1412_1840_gb300 as cp
+from oracle.series import taylor_harmonic_coefficients
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "cp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cp_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = cp.lib()
+    names = declared_functions()
+    assert "cp_plan" in names and "cp_periodogram" in names and "cp_best_period" in names
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_struct_sizes_match_header_layout():
+    assert ctypes.sizeof(cp.cp_freq_grid) == 56
+    assert ctypes.sizeof(cp.cp_options) == 48
+    o = cp.cp_default_options()
+    assert o.sigma_t == pytest.approx(0.3) and o.alpha == 1.0 and o.use_graph == 1
+    assert o.form == cp.CP_FORM_DIRECT and o.input_memory == cp.CP_MEM_HOST
+
+
+def test_status_strings():
+    L = cp.lib()
+    for s in range(7):
+        assert L.cp_status_string(s)
+
+
+@pytest.mark.parametrize("st,nm", [(0.6, 12), (0.3, 24), (0.15, 48), (0.1, 64)])
+def test_bessel_coefficients_match_taylor_series(st, nm):
+    a = cp.cp_bessel_coefficients(st, nm)
+    b = np.array(taylor_harmonic_coefficients(st, nm))
+    np.testing.assert_allclose(a, b, rtol=1e-11, atol=1e-15)
+    tail = 1.0 - a.sum()                       # sum over all harmonics is the kernel peak, 1
+    assert 0.0 <= tail < 2e-3
+    assert np.all(np.diff(a[1:]) < 0)           # a_n = 2 e^-k I_n(k) decreases in n
+
+
+def _plan_status(offsets, grid=None, **kw):
+    n = int(offsets[-1])
+    t = np.arange(max(n, 1), dtype=np.float64)
+    m = np.zeros(max(n, 1), np.float32)
+    e = np.ones(max(n, 1), np.float32)
+    g = grid or cp.make_grid(0.01, 0.01, 10)
+    try:
+        cp.Plan(t, m, e, np.asarray(offsets, np.int64), g, **kw)
+    except cp.CpError as err:
+        return err.status
+    return cp.CP_OK
+
+
+def test_argument_validation_precedes_device_use():
+    assert _plan_status([0, 1]) == cp.CP_EINVAL                       # N < 2
+    assert _plan_status([1, 5]) == cp.CP_EINVAL                       # offsets[0] != 0
+    assert _plan_status([0, 5, 4]) == cp.CP_EINVAL                    # decreasing
+    assert _plan_status([0, cp.cp_max_points() + 1]) == cp.CP_EUNSUPPORTED
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.0, 10)) == cp.CP_EINVAL
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 0)) == cp.CP_EINVAL
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 10, True, 0.0, 3, 1e-3, 1e-2)) == cp.CP_EINVAL
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 10, True, 0.05, 0, 1e-3, 1e-2)) == cp.CP_EINVAL
+    assert _plan_status([0, 5], sigma_t=0.0) == cp.CP_EINVAL
+    assert _plan_status([0, 5], alpha=-1.0) == cp.CP_EINVAL
+    assert _plan_status([0, 5], sigma_t_mode=7) == cp.CP_EINVAL
+
+
+def test_no_device_is_an_error_not_a_fallback():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    assert _plan_status([0, 5]) == cp.CP_ECUDA

@@ -1,0 +1,243 @@
+"""Parity of the direct FP32 CUDA path against the FP64 oracle.
+
+The bar (arXiv:1412.1840 statistic, Eq. (CKP)): per curve,
+max_k |nCKP_gpu - nCKP_oracle| / max_k |nCKP_oracle| <= 1e-5, and the best
+index is accepted when nCKP_oracle(k_gpu) >= nCKP_oracle(k*) - 1e-5 |nCKP_oracle(k*)|
+(bit-exact agreement whenever the oracle's top two values differ by more).
+All calls go through the C ABI (include/cp.h) via the ctypes binding.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1412_1840_gb300 as cp  # noqa: E402
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def run_gpu(batch, grid, periodogram=True, **kw):
+    with cp.Plan(batch.times, batch.mags, batch.errs, batch.offsets, cp.grid_from(grid), **kw) as p:
+        out = None
+        if periodogram:
+            out = torch.empty((batch.n_curves, grid.n_freq), dtype=torch.float32, device="cuda")
+            p.periodogram(out)
+            p.sync()
+            out = out.cpu().numpy()
+        best = p.best_period()
+        stats = p.curve_stats()
+        info = p.info()
+    return out, best, stats, info
+
+
+def peak_rel_err(gpu, ref):
+    return np.max(np.abs(gpu - ref), axis=1) / np.max(np.abs(ref), axis=1)
+
+
+def check_best(best, ref, tol=TOL, rows=None):
+    """c16 acceptance of the GPU best index against the oracle periodogram rows."""
+    for c in (range(ref.shape[0]) if rows is None else rows):
+        kstar = int(np.argmax(ref[c]))
+        k = int(best["best_idx"][c])
+        vstar = ref[c, kstar]
+        assert ref[c, k] >= vstar - tol * abs(vstar) - 1e-30, (c, k, kstar)
+        srt = np.sort(ref[c])[::-1]
+        if srt.shape[0] > 1 and srt[0] - srt[1] > 2 * tol * abs(srt[0]):
+            assert k == kstar, (c, k, kstar)
+
+
+def test_edge_batch_periodogram():
+    b = synth.edge_batch()
+    g = synth.Grid(0.005, 0.005, 600)             # 37 chunks of 16 plus a tail of 8
+    out, best, stats, _ = run_gpu(b, g, sigma_t=0.3)
+    st = stats["sigma_t"].astype(np.float64)
+    ref = oracle.batch_nckp(b, st, g.freqs())
+    const = 3                                      # constant-magnitude curve: W == 0
+    assert np.all(out[const] == 0.0) and np.all(np.abs(ref[const]) < 1e-12)
+    keep = [c for c in range(b.n_curves) if c != const]
+    err = peak_rel_err(out[keep], ref[keep])
+    assert np.all(err <= TOL), err
+    check_best(best, ref, rows=keep)
+    assert best["best_idx"][const] == 0 and best["best_stat"][const] == 0.0
+
+
+@pytest.mark.parametrize("f_min", [0.002, 4.48])
+def test_ragged_batch_periodogram_rule_sigma_t(f_min):
+    b = synth.ragged_batch(8, seed=21)
+    g = synth.Grid(f_min, 1e-4, 520)
+    out, best, stats, _ = run_gpu(b, g, sigma_t_mode=cp.CP_SIGMA_T_RULE)
+    st = stats["sigma_t"].astype(np.float64)
+    ref = oracle.batch_nckp(b, st, g.freqs())
+    err = peak_rel_err(out, ref)
+    assert np.all(err <= TOL), err
+    check_best(best, ref)
+
+
+def test_curve_stats_match_oracle():
+    b = synth.ragged_batch(24, seed=22, n_lo=2, n_hi=700)
+    g = synth.Grid(0.01, 0.01, 40)
+    _, best, stats, _ = run_gpu(b, g, periodogram=False, sigma_t_mode=cp.CP_SIGMA_T_RULE, alpha=0.8)
+    ref = oracle.curve_stats(b, sigma_t_mode=2, alpha=0.8)
+    np.testing.assert_allclose(stats["sigma_y"], ref["sigma_y"], rtol=1e-7)
+    np.testing.assert_allclose(stats["psnr"], ref["psnr"], rtol=2e-7)
+    np.testing.assert_allclose(stats["sigma_t"], ref["sigma_t"], rtol=2e-7)
+    np.testing.assert_allclose(stats["ip"], ref["ip"], rtol=2e-6)
+    np.testing.assert_array_equal(best["psnr"], stats["psnr"])
+
+
+def test_discriminator_and_threshold_bins():
+    b = synth.ragged_batch(16, seed=23, n_lo=80, n_hi=200)
+    g = synth.Grid(0.01, 1e-3, 300)
+    out, best, stats, _ = run_gpu(b, g)
+    for c in range(b.n_curves):
+        th = oracle.threshold(float(stats["psnr"][c]))
+        assert bool(best["is_periodic"][c]) == (float(best["best_stat"][c]) > th)
+        assert best["best_stat"][c] == out[c].max()
+
+
+def test_hierarchical_search_matches_oracle():
+    b = synth.ragged_batch(6, seed=24, n_lo=100, n_hi=260, span=1200.0)
+    g = synth.Grid(0.01, 1e-4, 19901, hierarchical=True, coarse_df=4e-3, top_k=10, fine_df=1e-4,
+                   fine_halfwidth=4e-3)
+    _, best, stats, _ = run_gpu(b, g, periodogram=False)
+    st = stats["sigma_t"].astype(np.float64)
+    ref = oracle.batch_best(b, g, sigma_t_mode=1, sigma_t_per_curve=st)
+    for c in range(b.n_curves):
+        f_gpu = best["best_freq"][c]
+        t, y = _tyd(b, c)
+        v_or_at_gpu = oracle.nckp(t, y, _sigma_y(b, c), st[c], [f_gpu])[0]
+        vstar = ref["best_stat"][c]
+        assert v_or_at_gpu >= vstar - TOL * abs(vstar), (c, f_gpu, ref["best_freq"][c])
+        assert abs(best["best_stat"][c] - v_or_at_gpu) <= TOL * abs(vstar)
+        if best["best_idx"][c] == ref["best_idx"][c]:
+            assert f_gpu == ref["best_freq"][c]
+
+
+def _tyd(b, c):
+    t, m, _ = b.curve(c)
+    return t, m.astype(np.float64)
+
+
+def _sigma_y(b, c):
+    return oracle.median(b.curve(c)[2].astype(np.float64))
+
+
+def test_input_memory_graph_and_wave_variants_agree():
+    b = synth.ragged_batch(10, seed=25, n_lo=40, n_hi=400)
+    g = synth.Grid(0.02, 2e-3, 700, hierarchical=True, coarse_df=1e-2, top_k=4, fine_df=1e-3, fine_halfwidth=1e-2)
+    _, base, _, info = run_gpu(b, g, periodogram=False)
+    assert info["launches_per_search"] >= 6
+    # device-resident inputs
+    td = torch.from_numpy(b.times).cuda(); md = torch.from_numpy(b.mags).cuda(); ed = torch.from_numpy(b.errs).cuda()
+    with cp.Plan(td, md, ed, b.offsets, cp.grid_from(g)) as p:
+        dev = p.best_period()
+        dev2 = p.best_period()
+    # pinned host inputs, no graph
+    tp = torch.from_numpy(b.times).pin_memory(); mp = torch.from_numpy(b.mags).pin_memory()
+    ep = torch.from_numpy(b.errs).pin_memory()
+    with cp.Plan(tp, mp, ep, b.offsets, cp.grid_from(g), use_graph=False) as p:
+        pin = p.best_period()
+    # several W waves
+    os.environ["CP_W_BUDGET_KB"] = "200"
+    try:
+        _, waves, _, winfo = run_gpu(b, g, periodogram=False)
+    finally:
+        del os.environ["CP_W_BUDGET_KB"]
+    assert winfo["launches_per_search"] > info["launches_per_search"]
+    for r in (dev, dev2, pin, waves):
+        np.testing.assert_array_equal(r["best_idx"], base["best_idx"])
+        np.testing.assert_array_equal(r["best_freq"], base["best_freq"])
+        np.testing.assert_array_equal(r["best_stat"], base["best_stat"])
+        np.testing.assert_array_equal(r["is_periodic"], base["is_periodic"])
+
+
+def test_time_shift_invariance():
+    b = synth.ragged_batch(4, seed=26, n_lo=50, n_hi=300)
+    g = synth.Grid(0.01, 1e-3, 333)
+    out0, _, _, _ = run_gpu(b, g)
+    b2 = synth.Batch(b.times + 2451234.5, b.mags, b.errs, b.offsets, b.period, b.periodic, b.kind)
+    out1, _, _, _ = run_gpu(b2, g)
+    assert np.all(peak_rel_err(out1, out0.astype(np.float64)) <= 2e-6)
+
+
+def test_invalid_values_are_reported():
+    b = synth.ragged_batch(3, seed=27, n_lo=10, n_hi=20)
+    g = synth.Grid(0.01, 1e-2, 50)
+    bad = synth.Batch(b.times, b.mags.copy(), b.errs, b.offsets, b.period, b.periodic, b.kind)
+    bad.mags[5] = np.nan
+    with cp.Plan(bad.times, bad.mags, bad.errs, bad.offsets, cp.grid_from(g)) as p:
+        with pytest.raises(cp.CpError) as ei:
+            p.best_period()
+        assert ei.value.status == cp.CP_EINVAL
+    zero = synth.Batch(b.times, b.mags, np.zeros_like(b.errs), b.offsets, b.period, b.periodic, b.kind)
+    with cp.Plan(zero.times, zero.mags, zero.errs, zero.offsets, cp.grid_from(g)) as p:
+        with pytest.raises(cp.CpError):
+            p.best_period()
+
+
+def test_full_size_ragged_batch_sampled():
+    """4096 curves, N ~ U{300..1000}, 49,981 frequencies (the benchmark's
+    workload and launch configuration): sampled periodogram values and the
+    best period of sampled curves against the oracle."""
+    b, g = synth.workload_ragged()
+    td = torch.from_numpy(b.times).cuda(); md = torch.from_numpy(b.mags).cuda(); ed = torch.from_numpy(b.errs).cuda()
+    rng = np.random.default_rng(99)
+    curves = np.sort(rng.choice(b.n_curves, 6, replace=False))
+    with cp.Plan(td, md, ed, b.offsets, cp.grid_from(g), sigma_t_mode=cp.CP_SIGMA_T_RULE) as p:
+        best = p.best_period()
+        out = torch.empty((b.n_curves, g.n_freq), dtype=torch.float32, device="cuda")
+        p.periodogram(out)
+        p.sync()
+        stats = p.curve_stats()
+        rows = out[torch.from_numpy(curves).cuda()].cpu().numpy()
+    del out
+    f = g.freqs()
+    for r, c in enumerate(curves):
+        assert best["best_stat"][c] == rows[r].max()
+        assert best["best_idx"][c] == int(np.argmax(rows[r]))
+        ks = np.unique(np.concatenate([rng.choice(g.n_freq, 48, replace=False),
+                                       np.clip(best["best_idx"][c] + np.arange(-8, 9), 0, g.n_freq - 1)]))
+        t, y = _tyd(b, c)
+        ref = oracle.nckp(t, y, _sigma_y(b, c), float(stats["sigma_t"][c]), f[ks])
+        peak = max(abs(ref).max(), abs(rows[r]).max())
+        assert np.max(np.abs(rows[r][ks] - ref)) <= TOL * peak, c
+        # the GPU best is a local maximum of the oracle within tolerance
+        kb = int(best["best_idx"][c])
+        loc = ks[np.abs(ks - kb) <= 8]
+        assert ref[np.searchsorted(ks, kb)] >= ref[np.isin(ks, loc)].max() - TOL * peak
+
+
+def test_full_size_hierarchical_sampled():
+    """Same batch with the coarse-then-fine search (coarse 1e-3, top-10,
+    fine 1e-5 over +-2e-3): sampled curves' best frequency and value."""
+    b, g = synth.workload_hierarchical()
+    td = torch.from_numpy(b.times).cuda(); md = torch.from_numpy(b.mags).cuda(); ed = torch.from_numpy(b.errs).cuda()
+    with cp.Plan(td, md, ed, b.offsets, cp.grid_from(g), sigma_t_mode=cp.CP_SIGMA_T_RULE) as p:
+        best = p.best_period()
+        stats = p.curve_stats()
+        info = p.info()
+    assert info["pair_freq_search"] > 8e12
+    rng = np.random.default_rng(98)
+    for c in np.sort(rng.choice(b.n_curves, 6, replace=False)):
+        t, y = _tyd(b, c)
+        fb = best["best_freq"][c]
+        J = 200
+        j = int(best["best_idx"][c]) % (2 * J + 1) - J
+        offs = np.array([o for o in range(-3, 4) if abs(j + o) <= J])   # stay inside the window
+        ref = oracle.nckp(t, y, _sigma_y(b, c), float(stats["sigma_t"][c]), fb + offs * g.fine_df)
+        peak = abs(ref).max()
+        at = int(np.nonzero(offs == 0)[0][0])
+        assert abs(best["best_stat"][c] - ref[at]) <= TOL * peak
+        assert ref[at] >= ref.max() - TOL * peak       # best among its evaluated window neighbours
