@@ -235,7 +235,9 @@ def test_full_size_hierarchical_sampled():
         fb = best["best_freq"][c]
         J = 200
         j = int(best["best_idx"][c]) % (2 * J + 1) - J
-        offs = np.array([o for o in range(-3, 4) if abs(j + o) <= J])   # stay inside the window
+        # stay inside the window and the searched band [f_min, f_max]
+        offs = np.array([o for o in range(-3, 4)
+                         if abs(j + o) <= J and g.f_min <= fb + o * g.fine_df <= g.f_max])
         ref = oracle.nckp(t, y, _sigma_y(b, c), float(stats["sigma_t"][c]), fb + offs * g.fine_df)
         peak = abs(ref).max()
         at = int(np.nonzero(offs == 0)[0][0])
