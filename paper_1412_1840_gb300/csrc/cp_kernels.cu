@@ -252,7 +252,8 @@ __global__ void __launch_bounds__(256) k_build_w(const BuildWArgs a)
 // ===========================================================================
 // k_pair_direct: persistent CTAs pop (curve, frequency-chunk) units.
 // ===========================================================================
-constexpr int kPairThreads = 256;
+constexpr int kPairThreads = 512;
+constexpr int kHalfRows = kRowsPerLane / 2;   // rows per lane in a half-tile work item
 
 __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs a)
 {
@@ -328,23 +329,37 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
 
         const int nb = npad / kTile;
         const int ntiles = nb * (nb + 1) / 2;
-        const float* Wc = a.W + (a.wtile_start[slot] - a.wtile_base) * kTileFloats;
-        f2 accF[kFcMax / 2], accG[kFcMax / 2];   // per f-pair: frequency f (accF) and f' (accG)
+        const int nitems = 2 * ntiles;           // (tile, row half): 16 x 32 pairs per warp item
+        const float4* Wc = reinterpret_cast<const float4*>(a.W + (a.wtile_start[slot] - a.wtile_base) * kTileFloats);
+        f2 acc[kFcMax / 2];                      // per f-pair: (sum at f, sum at f')
 #pragma unroll
-        for (int q = 0; q < kFcMax / 2; q++) { accF[q] = 0ull; accG[q] = 0ull; }
+        for (int q = 0; q < kFcMax / 2; q++) acc[q] = 0ull;
 
-        for (int t = warp; t < ntiles; t += NW) {
-            int bi, bj;
-            decode_tile(t, nb, bi, bj);
-            const float4* Wt = reinterpret_cast<const float4*>(Wc + (int64_t)t * kTileFloats);
-            f2 w01[kRowsPerLane], w23[kRowsPerLane];
+        // W of the first item; each item prefetches the next one's
+        float4 wn[kHalfRows];
+        int item = warp;
+        if (item < nitems) {
 #pragma unroll
-            for (int k = 0; k < kRowsPerLane; k++) {
-                const float4 v = __ldg(Wt + k * 32 + lane);
-                w01[k] = pk(v.x, v.y);
-                w23[k] = pk(v.z, v.w);
+            for (int k = 0; k < kHalfRows; k++)
+                wn[k] = __ldg(Wc + (int64_t)(item >> 1) * (kTileFloats / 4) + ((item & 1) * kHalfRows + k) * 32 + lane);
+        }
+#pragma unroll 1
+        for (; item < nitems; item += NW) {
+            f2 w01[kHalfRows], w23[kHalfRows];
+#pragma unroll
+            for (int k = 0; k < kHalfRows; k++) {
+                w01[k] = pk(wn[k].x, wn[k].y);
+                w23[k] = pk(wn[k].z, wn[k].w);
             }
-            const int rbase = bi * kTile + la;
+            const int nxt = item + NW;
+            if (nxt < nitems) {
+#pragma unroll
+                for (int k = 0; k < kHalfRows; k++)
+                    wn[k] = __ldg(Wc + (int64_t)(nxt >> 1) * (kTileFloats / 4) + ((nxt & 1) * kHalfRows + k) * 32 + lane);
+            }
+            int bi, bj;
+            decode_tile(item >> 1, nb, bi, bj);
+            const int rbase = bi * kTile + (item & 1) * (kTile / 2) + la;
             const int cbase = bj * kTile + lb;
 #pragma unroll
             for (int fp = 0; fp < kFcMax / 2; fp++) {
@@ -356,7 +371,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
                     for (int m = 0; m < kColsPerLane; m++) col[m] = SCf[cbase + 8 * m];
                     f2 tf0 = 0ull, tf1 = 0ull, tg0 = 0ull, tg1 = 0ull;
 #pragma unroll
-                    for (int k = 0; k < kRowsPerLane; k++) {
+                    for (int k = 0; k < kHalfRows; k++) {
                         const int i = rbase + 4 * k;
                         const f2 A = SCf[i].y;   // (c_i(f), c_i(f'))
                         const f2 B = NSf[i];     // (-s_i(f), -s_i(f'))
@@ -376,8 +391,10 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
                         tg0 = fma2(w01[k], pk(e[0][1], e[1][1]), tg0);
                         tg1 = fma2(w23[k], pk(e[2][1], e[3][1]), tg1);
                     }
-                    accF[fp] = add2(accF[fp], add2(tf0, tf1));
-                    accG[fp] = add2(accG[fp], add2(tg0, tg1));
+                    float fx, fy, gx, gy;
+                    upk(add2(tf0, tf1), fx, fy);
+                    upk(add2(tg0, tg1), gx, gy);
+                    acc[fp] = add2(acc[fp], pk(fx + fy, gx + gy));
                 }
             }
         }
@@ -386,10 +403,8 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
 #pragma unroll
         for (int fp = 0; fp < kFcMax / 2; fp++) {
             if (fp < nfp) {
-                float a0, a1, b0, b1;
-                upk(accF[fp], a0, a1);
-                upk(accG[fp], b0, b1);
-                float vf = a0 + a1, vg = b0 + b1;
+                float vf, vg;
+                upk(acc[fp], vf, vg);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     vf += __shfl_xor_sync(0xffffffffu, vf, o);
