@@ -5,7 +5,7 @@
 //                  scaled magnitudes y' and 64-bit fixed-point phase steps
 //   k_build_w      period-independent magnitude-kernel tiles w_ij = g_ij - ip
 //   k_pair_direct  persistent pair-sum kernel over (curve, frequency-chunk)
-//                  work units: the N(N-1)/2 interactions of Section 7 per
+//                  work units: the N(N-1)/2 interactions of Section 8 per
 //                  trial frequency, FP32 with packed f32x2 arithmetic
 //   k_topk         coarse-grid local maxima for the coarse-then-fine search
 //   k_finalize     best frequency, nCKP and Table tab:th discriminator
