@@ -16,7 +16,7 @@
  * curve, or from the Bowley-skewness rule of Section 3.  The best period is
  * the argmax of nCKP over the trial frequencies (Section 3), and a curve is
  * labelled periodic when nCKP(best) exceeds th(pSNR) of Table tab:th with
- * pSNR = 0.7413 iqr(y) / (alpha med(e)) (Eq. (pSNR), Section 4.1).
+ * pSNR = 0.7413 iqr(y) / (alpha med(e)) (Eq. (pSNR), Section 5.2).
  *
  * All entry points return a cp_status and never throw.  On failure
  * cp_last_error() returns a thread-local message.  Nothing is computed on
@@ -190,6 +190,44 @@ int64_t cp_max_points(void);
  * Computed in FP64 by the trapezoid rule on (1/pi) int_0^pi e^{k(cos t - 1)} cos(n t) dt.
  */
 cp_status cp_bessel_coefficients(double sigma_t, int32_t n_max, double *out);
+
+/*
+ * cp_best_period_noalloc -- the best-period search for callers that cannot
+ * allocate device memory at the time of the call.  The paper has no
+ * counterpart: this is an interface for hosts that reserve all device memory
+ * for their own pools at start-up, latency-bounded pipelines that must not
+ * enter the allocator, or plug-ins whose host owns the allocator.
+ *
+ * It runs the direct form (same kernels and results as cp_best_period with
+ * CP_FORM_DIRECT, CP_SIGMA_T_FIXED, alpha = 1) and allocates nothing: every
+ * intermediate buffer lives in one static device array of
+ * CP_NOALLOC_SCRATCH_BYTES that each GPU loading the library holds until the
+ * process exits.  Its first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current.
+ *
+ *   times, mags, errs   DEVICE arrays, CSR layout as in cp_plan.
+ *   offsets             HOST int64, n_curves+1 entries, offsets[0] = 0.
+ *   n_curves            1 .. CP_NOALLOC_MAX_CURVES; the whole batch must fit
+ *                       the scratch array (CP_EUNSUPPORTED otherwise).
+ *   grid                as in cp_plan (full or coarse-then-fine).
+ *   sigma_t             fixed periodic-kernel size, > 0.
+ *   cuda_stream         stream of the current device (NULL = legacy default).
+ *   best_idx, best_freq, best_stat, is_periodic
+ *                       DEVICE arrays of n_curves entries (any may be NULL),
+ *                       meaning as in cp_best_period.
+ *
+ * Synchronous: returns after the results are written; CP_EINVAL then also
+ * reports non-finite inputs or a zero median error bar.  Every call uses the
+ * same scratch array, which keeps the last call's contents (the call clears
+ * what must start at zero): calls that overlap on the GPU -- from several
+ * host threads, or on several streams -- race and give wrong results.
+ */
+#define CP_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define CP_NOALLOC_MAX_CURVES 256
+cp_status cp_best_period_noalloc(const double *times, const float *mags, const float *errs,
+                                 const int64_t *offsets, int64_t n_curves, const cp_freq_grid *grid,
+                                 float sigma_t, void *cuda_stream, int64_t *best_idx, double *best_freq,
+                                 float *best_stat, uint8_t *is_periodic);
 
 const char *cp_status_string(cp_status s);
 const char *cp_last_error(void);

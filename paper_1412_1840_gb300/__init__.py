@@ -83,6 +83,9 @@ def _load():
         L.cp_destroy.restype = None
         L.cp_max_points.restype = i64
         L.cp_bessel_coefficients.argtypes = [d, ctypes.c_int32, vp]
+        L.cp_best_period_noalloc.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(cp_freq_grid), ctypes.c_float, vp,
+                                             vp, vp, vp, vp]
+        L.cp_best_period_noalloc.restype = ctypes.c_int
         L.cp_status_string.argtypes = [ctypes.c_int]
         L.cp_status_string.restype = ctypes.c_char_p
         L.cp_last_error.restype = ctypes.c_char_p
@@ -275,6 +278,35 @@ def cp_get_plan_info(plan: Plan):
 
 def cp_destroy(plan: Plan):
     plan.close()
+
+
+def cp_best_period_noalloc(times, mags, errs, offsets, grid: cp_freq_grid, sigma_t: float, best_idx=None,
+                           best_freq=None, best_stat=None, is_periodic=None, stream=None):
+    """Best-period search that allocates no device memory (for callers that
+    cannot allocate at call time).  Inputs and outputs are CUDA tensors on
+    the current device (outputs: int64, float64, float32, uint8; any may be
+    None); offsets is a host int64 array.  Synchronous."""
+    pt, dt, _ = _ptr(times)
+    pm, dm, _ = _ptr(mags)
+    pe, de, _ = _ptr(errs)
+    if not (dt and dm and de):
+        raise ValueError("times, mags and errs must be CUDA tensors")
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    outs = []
+    for o in (best_idx, best_freq, best_stat, is_periodic):
+        if o is None:
+            outs.append(None)
+            continue
+        po, on_dev, _ = _ptr(o)
+        if not on_dev:
+            raise ValueError("outputs must be CUDA tensors")
+        outs.append(po)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(_load().cp_best_period_noalloc(pt, pm, pe, off.ctypes.data, int(off.shape[0] - 1), ctypes.byref(grid),
+                                          float(sigma_t), ctypes.c_void_p(stream) if stream else None, *outs),
+           "cp_best_period_noalloc")
 
 
 def grid_from(g) -> cp_freq_grid:

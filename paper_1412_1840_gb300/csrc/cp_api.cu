@@ -22,15 +22,26 @@
 
 using namespace cpk;
 
+namespace cpk {
+
 namespace {
+thread_local char g_last_error[512];
+}
 
-thread_local std::string g_last_error;
+const char* last_error_buffer() { return g_last_error; }
 
-cp_status fail(cp_status s, const std::string& msg)
+cp_status set_error(cp_status s, const char* msg)
 {
-    g_last_error = msg;
+    std::strncpy(g_last_error, msg ? msg : "", sizeof(g_last_error) - 1);
+    g_last_error[sizeof(g_last_error) - 1] = 0;
     return s;
 }
+
+}  // namespace cpk
+
+namespace {
+
+cp_status fail(cp_status s, const std::string& msg) { return cpk::set_error(s, msg.c_str()); }
 
 // A failed runtime call also sets the runtime's per-thread last error; it is
 // cleared here so that it cannot surface later in unrelated CUDA code.
@@ -418,7 +429,7 @@ const char* cp_status_string(cp_status s)
     return "unknown status";
 }
 
-const char* cp_last_error(void) { return g_last_error.c_str(); }
+const char* cp_last_error(void) { return cpk::last_error_buffer(); }
 
 void cp_destroy(cp_plan_t p)
 {
@@ -712,9 +723,11 @@ cp_status cp_plan(const double* times, const float* mags, const float* errs, con
     cp_status st = plan_impl(times, mags, errs, offsets, n_curves, grid, opt, stream, p);
     cudaSetDevice(prev);
     if (st != CP_OK) {
-        std::string msg = g_last_error;
+        char msg[512];
+        std::strncpy(msg, cpk::last_error_buffer(), sizeof(msg) - 1);
+        msg[sizeof(msg) - 1] = 0;
         cp_destroy(p);
-        g_last_error = msg;
+        cpk::set_error(st, msg);
         return st;
     }
     *out_plan = p;

@@ -19,6 +19,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "cp.h"
+
 namespace cpk {
 
 constexpr int kMaxN = 4096;            // largest curve the kernels accept
@@ -155,6 +157,10 @@ int pair_direct_threads();
 cudaError_t pair_direct_occupancy(int* blocks_per_sm, size_t smem);
 size_t stats_smem_bytes(int np2max);
 cudaError_t prepare_kernels(int np2max, size_t pair_smem);
+
+// Thread-local message returned by cp_last_error() (fixed buffer, no heap).
+cp_status set_error(cp_status s, const char* msg);
+const char* last_error_buffer();
 
 // ---------------------------------------------------------------------------
 // FP64-exact phase in 64-bit fixed point: frac(a * b) * 2^64 (mod 2^64).
