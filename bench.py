@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="ragged", choices=["ragged", "hierarchical", "single", "small"])
     ap.add_argument("--n-curves", type=int, default=None)
     ap.add_argument("--form", default="direct", choices=["direct", "tensor"])
+    ap.add_argument("--n-max", type=int, default=16, help="harmonics of the tensor form")
+    ap.add_argument("--dtype", default="fp16", choices=["fp16", "bf16"], help="tensor-form operand type")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
@@ -214,8 +216,9 @@ def main():
     td = torch.from_numpy(b.times).to(dev)
     md = torch.from_numpy(b.mags).to(dev)
     ed = torch.from_numpy(b.errs).to(dev)
+    tkw = dict(n_max=args.n_max, dtype=cp.CP_DTYPE_BF16 if args.dtype == "bf16" else cp.CP_DTYPE_FP16)
     plan = cp.Plan(td, md, ed, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=form,
-                   device=local, stream=stream.cuda_stream)
+                   device=local, stream=stream.cuda_stream, **tkw)
     n = b.n_curves
     idx = np.empty(n, np.int64); bf = np.empty(n, np.float64); bs = np.empty(n, np.float32)
     per = np.empty(n, np.uint8); ps = np.empty(n, np.float32)
@@ -250,7 +253,7 @@ def main():
         mp = torch.from_numpy(b.mags).pin_memory()
         ep = torch.from_numpy(b.errs).pin_memory()
         hplan = cp.Plan(tp, mp, ep, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=form,
-                        device=local, stream=stream.cuda_stream)
+                        device=local, stream=stream.cuda_stream, **tkw)
         hplan.best_period_into(idx, bf, bs, per, ps)
         e_steps = max(1, min(args.steps, 2))
         barrier()

@@ -104,6 +104,11 @@ struct cp_plan_s {
     std::vector<Wave> waves;
     size_t pair_smem = 0;
     int pair_grid = 0;
+    bool tensor = false;               // CP_FORM_TENSOR
+    uint32_t wait_limit = 1u << 26;    // polls per bounded device wait (tensor form)
+    int n_max = 0;                     // harmonics of the tensor form
+    void* d_W16 = nullptr;             // pre-swizzled W' tiles (tensor form)
+    float* d_coef = nullptr;           // [n_curves * n_max]
 
     // device buffers
     void* dblock = nullptr;              // one allocation for everything below
@@ -218,6 +223,7 @@ cp_status enqueue_stats(cp_plan_t p, cudaStream_t s)
     a.np2max = p->np2max;
     a.status = reinterpret_cast<int*>(status_word(p));
     CP_CUDA(launch_stats(a, (int)p->n_curves, s));
+    if (p->tensor) CP_CUDA(launch_harmonic_coef(p->d_cp, (int)p->n_curves, p->n_max, p->d_coef, s));
     return CP_OK;
 }
 
@@ -276,6 +282,21 @@ PairArgs pair_args(cp_plan_t p, int stage, int w, float* out)
 cp_status enqueue_wave_w(cp_plan_t p, int w, cudaStream_t s)
 {
     const Wave& wv = p->waves[w];
+    if (p->tensor) {
+        BuildW16Args b{};
+        b.cp = p->d_cp;
+        b.order = p->d_order;
+        b.wtile_start = p->d_wtile;
+        b.yp = p->d_yp;
+        b.W16 = p->d_W16;
+        b.slot_begin = wv.slot_begin;
+        b.slot_end = wv.slot_end;
+        b.tile_begin = wv.tile_begin;
+        b.tile_end = wv.tile_end;
+        b.bf16 = p->opt.dtype == CP_DTYPE_BF16 ? 1 : 0;
+        CP_CUDA(launch_build_w16(b, s));
+        return CP_OK;
+    }
     BuildWArgs b{};
     b.cp = p->d_cp;
     b.order = p->d_order;
@@ -290,11 +311,52 @@ cp_status enqueue_wave_w(cp_plan_t p, int w, cudaStream_t s)
     return CP_OK;
 }
 
+TensorArgs tensor_args(const PairArgs& d, cp_plan_t p)
+{
+    TensorArgs t{};
+    t.cp = d.cp;
+    t.order = d.order;
+    t.unit_start = d.unit_start;
+    t.wtile_start = d.wtile_start;
+    t.W16 = p->d_W16;
+    t.coef = p->d_coef;
+    t.ph_base = d.ph_base;
+    t.ph_step = d.ph_step;
+    t.ph_coarse = d.ph_coarse;
+    t.peaks = d.peaks;
+    t.n_peaks = d.n_peaks;
+    t.stage = d.stage;
+    t.slot_begin = d.slot_begin;
+    t.slot_end = d.slot_end;
+    t.unit_begin = d.unit_begin;
+    t.unit_end = d.unit_end;
+    t.wtile_base = d.wtile_base;
+    t.n_freq = d.n_freq;
+    t.top_k = d.top_k;
+    t.fine_half = d.fine_half;
+    t.n_max = p->n_max;
+    t.bf16 = p->opt.dtype == CP_DTYPE_BF16 ? 1 : 0;
+    t.f_min = d.f_min;
+    t.f_max = d.f_max;
+    t.step = d.step;
+    t.coarse_df = d.coarse_df;
+    t.out = d.out;
+    t.out_ld = d.out_ld;
+    t.coarse_out = d.coarse_out;
+    t.best_key = d.best_key;
+    t.status = reinterpret_cast<int*>(status_word(p));
+    t.wait_limit = p->wait_limit;
+    return t;
+}
+
 cp_status enqueue_pair(cp_plan_t p, int stage, int w, float* out, cudaStream_t s, int* ev_idx)
 {
     const PairArgs a = pair_args(p, stage, w, out);
     if (ev_idx) CP_CUDA(cudaEventRecordWithFlags(p->ev_pair[2 * (*ev_idx)], s, rec_flags(p)));
-    CP_CUDA(launch_pair_direct(a, p->pair_grid, p->pair_smem, s));
+    if (p->tensor)
+        CP_CUDA(launch_pair_tensor(tensor_args(a, p), p->pair_grid, s));
+    else
+        CP_CUDA(launch_pair_direct(a, p->pair_grid, p->pair_smem, s));
     if (ev_idx) {
         CP_CUDA(cudaEventRecordWithFlags(p->ev_pair[2 * (*ev_idx) + 1], s, rec_flags(p)));
         (*ev_idx)++;
@@ -460,8 +522,19 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         return fail(CP_EINVAL, "cp_plan: n_curves must be in [1, 2^30]");
     cp_options opt;
     if (opt_in) opt = *opt_in; else cp_default_options(&opt);
-    if (opt.form != CP_FORM_DIRECT)
-        return fail(CP_EUNSUPPORTED, "cp_plan: only the direct form is built in this library version");
+    if (opt.form != CP_FORM_DIRECT && opt.form != CP_FORM_TENSOR)
+        return fail(CP_EINVAL, "cp_plan: form must be CP_FORM_DIRECT or CP_FORM_TENSOR");
+    if (opt.form == CP_FORM_TENSOR) {
+        if (opt.dtype != CP_DTYPE_FP16 && opt.dtype != CP_DTYPE_BF16)
+            return fail(CP_EINVAL, "cp_plan: dtype must be CP_DTYPE_FP16 or CP_DTYPE_BF16");
+        if (opt.n_max == 0) opt.n_max = 16;
+        if (opt.n_max != 4 && opt.n_max != 8 && opt.n_max != 16 && opt.n_max != 32)
+            return fail(CP_EINVAL, "cp_plan: n_max must be 0, 4, 8, 16 or 32");
+        p->tensor = true;
+        p->n_max = opt.n_max;
+        // test hook: shorter bounded waits, to exercise the timeout path
+        if (const char* env = std::getenv("CP_WAIT_LIMIT")) p->wait_limit = (uint32_t)std::strtoul(env, nullptr, 10);
+    }
     if (opt.sigma_t_mode < 0 || opt.sigma_t_mode > 2)
         return fail(CP_EINVAL, "cp_plan: sigma_t_mode must be 0, 1 or 2");
     if (opt.sigma_t_mode == CP_SIGMA_T_FIXED && !(opt.sigma_t > 0.f && std::isfinite(opt.sigma_t)))
@@ -563,7 +636,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     for (int64_t s = 0; s < n_curves; s++) {
         const int c = p->order[s];
         const int n = (int)(offsets[c + 1] - offsets[c]);
-        const int f = p->fc[c];
+        const int f = p->tensor ? 128 / p->n_max : p->fc[c];
         const double pairs = 0.5 * (double)n * (double)(n - 1);
         p->unit_full[s + 1] = p->unit_full[s] + (g.n_freq + f - 1) / f;
         if (g.hierarchical) {
@@ -574,9 +647,9 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             pf_search += pairs * (double)g.n_freq;
         }
         pf_full += pairs * (double)g.n_freq;
-        p->wtile[s + 1] = p->wtile[s] + tiles_of(n);
+        p->wtile[s + 1] = p->wtile[s] + (p->tensor ? tensor_tiles_of(n) : tiles_of(n));
         const size_t npad = (size_t)((n + kTile - 1) / kTile * kTile);
-        smem = std::max(smem, npad * (size_t)f * 12);
+        smem = std::max(smem, npad * (size_t)p->fc[c] * 12);   // direct-form trig table
     }
     p->pf_full = pf_full;
     p->pf_search = pf_search;
@@ -587,7 +660,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     CP_CUDA(cudaMemGetInfo(&free_b, &total_b));
     size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 3);
     if (const char* env = std::getenv("CP_W_BUDGET_KB")) budget = (size_t)std::atoll(env) << 10;
-    const int64_t tile_budget = std::max<int64_t>(1, (int64_t)(budget / (kTileFloats * sizeof(float))));
+    const size_t tile_bytes = p->tensor ? (size_t)128 * 64 * 2 : kTileFloats * sizeof(float);
+    const int64_t tile_budget = std::max<int64_t>(1, (int64_t)(budget / tile_bytes));
     int64_t max_wave_tiles = 0;
     {
         int sb = 0;
@@ -625,7 +699,9 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         {(void**)&p->d_unit_coarse, (nc + 1) * sizeof(int64_t)},
         {(void**)&p->d_unit_fine, (nc + 1) * sizeof(int64_t)},
         {(void**)&p->d_wtile, (nc + 1) * sizeof(int64_t)},
-        {(void**)&p->d_W, (size_t)max_wave_tiles * kTileFloats * sizeof(float)},
+        {(void**)&p->d_W, p->tensor ? 0 : (size_t)max_wave_tiles * kTileFloats * sizeof(float)},
+        {(void**)&p->d_W16, p->tensor ? (size_t)max_wave_tiles * tile_bytes : 0},
+        {(void**)&p->d_coef, p->tensor ? (size_t)nc * p->n_max * sizeof(float) : 0},
         {(void**)&p->d_coarse, hier ? (size_t)nc * p->kc * sizeof(float) : 0},
         {(void**)&p->d_peaks, hier ? (size_t)nc * g.top_k * sizeof(int32_t) : 0},
         {(void**)&p->d_npeaks, hier ? nc * sizeof(int32_t) : 0},
@@ -695,9 +771,14 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
 
     // launch geometry of the persistent pair kernel
     CP_CUDA(prepare_kernels(p->np2max, p->pair_smem));
-    int occ = 1;
-    CP_CUDA(pair_direct_occupancy(&occ, p->pair_smem));
-    p->pair_grid = p->n_sm * std::max(occ, 1);
+    if (p->tensor) {
+        CP_CUDA(prepare_tensor_kernel(p->n_max));
+        p->pair_grid = p->n_sm;    // one CTA per SM: 193 KB of shared memory and all 512 TMEM columns
+    } else {
+        int occ = 1;
+        CP_CUDA(pair_direct_occupancy(&occ, p->pair_smem));
+        p->pair_grid = p->n_sm * std::max(occ, 1);
+    }
 
     // events
     const int pair_launches = (int)p->waves.size() * (g.hierarchical ? 2 : 1);
@@ -706,7 +787,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     CP_CUDA(cudaEventCreate(&p->ev_step0));
     CP_CUDA(cudaEventCreate(&p->ev_step1));
     p->launches_per_search =
-        2 /* zero, stats */ + (int64_t)p->waves.size() * (g.hierarchical ? 4 : 2) + 1 /* finalize */;
+        2 /* zero, stats */ + (p->tensor ? 1 : 0) /* harmonic coefficients */ +
+        (int64_t)p->waves.size() * (g.hierarchical ? 4 : 2) + 1 /* finalize */;
     return CP_OK;
 }
 
@@ -762,6 +844,8 @@ static cp_status sync_impl(cp_plan_t p)
     if (!p) return fail(CP_EINVAL, "cp_sync: NULL plan");
     CP_CUDA(cudaSetDevice(p->device));
     CP_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->ran && (*p->h_status & 2))
+        return fail(CP_ETIMEOUT, "a bounded device wait of the tensor-core kernel gave up");
     if (p->ran && *p->h_status)
         return fail(CP_EINVAL, "input contains a non-finite value, a zero median error bar or a bad sigma_t");
     return CP_OK;
@@ -801,6 +885,7 @@ static cp_status best_period_impl(cp_plan_t p, int64_t* best_idx, double* best_f
     if (is_periodic) std::memcpy(is_periodic, p->h_res_per, nc);
     if (psnr) std::memcpy(psnr, p->h_res_psnr, nc * sizeof(float));
     cudaSetDevice(prev);
+    if (*p->h_status & 2) return fail(CP_ETIMEOUT, "a bounded device wait of the tensor-core kernel gave up");
     if (*p->h_status)
         return fail(CP_EINVAL, "input contains a non-finite value, a zero median error bar or a bad sigma_t");
     return CP_OK;

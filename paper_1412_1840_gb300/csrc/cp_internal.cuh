@@ -146,6 +146,55 @@ struct FinalArgs {
     float* psnr;
 };
 
+// Tensor form (cp_tensor.cu).
+struct BuildW16Args {
+    const CurveParams* cp;
+    const int32_t* order;
+    const int64_t* wtile_start;   // first W' tile of each slot (128 x 64 tiles)
+    const float* yp;
+    void* W16;
+    int slot_begin, slot_end;
+    int64_t tile_begin, tile_end;
+    int bf16;
+};
+
+struct TensorArgs {
+    const CurveParams* cp;
+    const int32_t* order;
+    const int64_t* unit_start;
+    const int64_t* wtile_start;
+    const void* W16;
+    const float* coef;            // [n_curves * n_max] a_1 .. a_nmax
+    const uint64_t* ph_base;
+    const uint64_t* ph_step;
+    const uint64_t* ph_coarse;
+    const int32_t* peaks;
+    const int32_t* n_peaks;
+    int stage;
+    int slot_begin, slot_end;
+    int64_t unit_begin, unit_end;
+    int64_t wtile_base;
+    int64_t n_freq;
+    int32_t top_k;
+    int32_t fine_half;
+    int32_t n_max;
+    int32_t bf16;
+    double f_min, f_max, step, coarse_df;
+    float* out;
+    int64_t out_ld;
+    float* coarse_out;
+    unsigned long long* best_key;
+    int* status;
+    uint32_t wait_limit;          // polls before a wait gives up (CP_ETIMEOUT)
+};
+
+size_t tensor_smem_bytes();
+int tensor_tiles_of(int n);
+cudaError_t prepare_tensor_kernel(int n_max);
+cudaError_t launch_build_w16(const BuildW16Args& a, cudaStream_t s);
+cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max, float* coef, cudaStream_t s);
+cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s);
+
 // Launchers (cp_kernels.cu); return the launch error.
 cudaError_t launch_stats(const StatsArgs& a, int n_curves, cudaStream_t s);
 cudaError_t launch_build_w(const BuildWArgs& a, cudaStream_t s);

@@ -1,0 +1,563 @@
+// cp_tensor.cu -- tensor-core form of the CKP pair sum (arXiv:1412.1840).
+//
+// Eq. (taylor) regrouped by harmonic gives
+//   exp(-2 sin^2(pi f dt) / st^2) = b_0 + sum_{n>=1} a_n cos(2 pi n f dt),
+//   a_n = 2 e^-k I_n(k), k = 1/st^2,
+// and since sum_ij w_ij = 0 (Eq. (IP)) the pair sum of Eq. (HP) becomes
+//   S(f) = sum_ij w_ij e_ij = sum_{n=1}^{n_max} a_n (c_n^T W c_n + s_n^T W s_n),
+//   c_{n,i} = cos(2 pi n f t_i), s_{n,i} = sin(2 pi n f t_i).
+// With W' = the upper block triangle of W in 128-row blocks (off-diagonal
+// blocks doubled), S(f) = sum_I z_I^T (W' Z)_I, so each work unit (curve, tile of
+// 256 columns = frequencies x harmonics x {cos, sin}) is a chain of GEMMs
+// D_I = W'[I, J >= I] * Z[J, cols] on tcgen05 (M = 128, N = 256, K = 64 per
+// stage, FP16 or BF16 operands, FP32 accumulation in TMEM), followed by the
+// epilogue q = sum_i Z[i, col] D_I[i, col] weighted by a_n.
+//
+// Warp roles (14 warps): warp 0 bulk-copies pre-swizzled W' tiles, warp 1
+// issues the MMAs, warps 2-5 read TMEM (epilogue), warps 6-13 generate the Z
+// tiles (cos/sin of every harmonic by the Chebyshev recurrence) straight into
+// the swizzled shared-memory layout the MMA reads.  Every wait is bounded.
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "cp_internal.cuh"
+#include "cp_tc.cuh"
+
+namespace cpk {
+
+using namespace tc;
+
+constexpr int kTcStages = 4;
+constexpr int kTcThreads = 448;
+constexpr int kTcA = 16384;            // 128 x 64 x 2 B
+constexpr int kTcB = 32768;            // 256 x 64 x 2 B
+constexpr int kTcCols = 256;           // columns per unit
+constexpr int kTcProducers = 256;      // warps 6..13
+constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr int kTcTablePoints = 1024;   // per-unit phase table in shared memory (producers)
+
+__host__ __device__ inline int tc_mtiles(int n) { return (n + 127) / 128; }
+__host__ __device__ inline int tc_kchunks(int n) { return (n + 63) / 64; }
+__host__ __device__ inline int tc_tiles_of(int n)
+{
+    const int nmt = tc_mtiles(n), nkc = tc_kchunks(n);
+    int t = 0;
+    for (int I = 0; I < nmt; I++) t += nkc - 2 * I > 0 ? nkc - 2 * I : 0;
+    return t;
+}
+__host__ __device__ inline int tc_tile_index(int I, int J, int nkc)
+{
+    // tiles stored I-major: sum_{I' < I} (nkc - 2 I') + (J - 2 I)
+    return I * nkc - I * (I - 1) + (J - 2 * I);
+}
+
+// sin(2 pi x), cos(2 pi x) for x = U / 2^32, exact quadrant handling.
+__device__ __forceinline__ void sincos2pi_turns(uint32_t U, float& s, float& c)
+{
+    const uint32_t q = ((U + 0x20000000u) >> 30) & 3u;      // nearest quarter turn
+    const int32_t r = (int32_t)(U - (q << 30));              // [-2^29, 2^29)
+    // reuse the pi-polynomial on the doubled residual: sin(2 pi r') = sin(pi (2 r'))
+    const uint32_t U2 = (uint32_t)(r * 2);                    // 2r' in turns of pi, |.| <= 1/4
+    float sx, cx;
+    sincospi_turns(U2, sx, cx);                               // n = 0 branch: exact for |x| <= 1/4
+    switch (q) {
+    case 0: s = sx; c = cx; break;
+    case 1: s = cx; c = -sx; break;
+    case 2: s = -sx; c = -cx; break;
+    default: s = -cx; c = sx; break;
+    }
+}
+
+__device__ __forceinline__ uint16_t to16(float v, bool bf)
+{
+    return bf ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+}
+
+// ===========================================================================
+// k_build_w16: pre-swizzled 128 x 64 tiles of W' (one CTA per tile).
+// ===========================================================================
+__global__ void __launch_bounds__(256) k_build_w16(const BuildW16Args a)
+{
+    const int64_t T = a.tile_begin + blockIdx.x;
+    if (T >= a.tile_end) return;
+    int lo = a.slot_begin, hi = a.slot_end - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.wtile_start[mid] <= T) lo = mid; else hi = mid - 1;
+    }
+    const int c = a.order[lo];
+    const CurveParams P = a.cp[c];
+    const int n = P.n, nkc = tc_kchunks(n);
+    int t = (int)(T - a.wtile_start[lo]);
+    int I = 0;
+    while (t >= nkc - 2 * I) { t -= nkc - 2 * I; ++I; }
+    const int J = 2 * I + t;
+    const float scale = (J >= 2 * I + 2) ? 2.0f : 1.0f;
+    const int r = threadIdx.x >> 1;                 // tile row
+    const int kb = (threadIdx.x & 1) * 32;          // first of 32 columns
+    const int i = I * 128 + r;
+    const float ypi = i < n ? a.yp[P.off + i] : 0.f;
+    unsigned char* dst = reinterpret_cast<unsigned char*>(a.W16) + (T - a.tile_begin) * (int64_t)kTcA;
+#pragma unroll
+    for (int ch = 0; ch < 4; ch++) {
+        uint32_t packed[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float v2[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int k = kb + ch * 8 + e + h;
+                const int j = J * 64 + k;
+                float w = 0.f;
+                if (i < n && j < n) w = ((gauss_g(ypi, a.yp[P.off + j]) - P.ip_hi) - P.ip_lo) * scale;
+                v2[h] = w;
+            }
+            packed[e >> 1] = (uint32_t)to16(v2[0], a.bf16) | ((uint32_t)to16(v2[1], a.bf16) << 16);
+        }
+        *reinterpret_cast<uint4*>(dst + sw128_offset(r, kb + ch * 8)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    }
+}
+
+// ===========================================================================
+// k_harmonic_coef: a_n = 2 e^-k I_n(k), n = 1..n_max, per curve (one warp),
+// trapezoid rule on (1/pi) int_0^pi e^{k(cos t - 1)} cos(n t) dt in FP64.
+// ===========================================================================
+__global__ void __launch_bounds__(256) k_harmonic_coef(const CurveParams* cp, int n_curves, int n_max, float* coef)
+{
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= n_curves) return;
+    const double st = (double)cp[c].sigma_t;
+    const double kap = 1.0 / (st * st);
+    const int M = 64 + 4 * (int)kap + 4 * n_max;
+    double acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; q++) acc[q] = 0.0;
+    for (int k = lane; k <= M; k += 32) {
+        const double th = CP_PI * (double)k / (double)M;
+        const double wgt = (k == 0 || k == M) ? 0.5 : 1.0;
+        const double ct = cos(th);
+        const double e = wgt * exp(kap * (ct - 1.0));
+        double cm2 = 1.0, cm1 = ct;   // cos(0 t), cos(1 t)
+#pragma unroll
+        for (int q = 0; q < 32; q++) {
+            if (q < n_max) acc[q] += e * cm1;
+            const double cn = 2.0 * ct * cm1 - cm2;
+            cm2 = cm1;
+            cm1 = cn;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 32; q++) {
+        double v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && q < n_max) coef[(int64_t)c * n_max + q] = (float)(2.0 * v / (double)M);
+    }
+}
+
+// ===========================================================================
+// k_pair_tensor
+// ===========================================================================
+struct TcUnit {
+    int c, n, nmt, nkc;
+    int64_t kfirst;
+    int count;
+    int peak;
+    uint64_t peak_mult;
+    int64_t wbase;      // first W' tile of the curve (relative to the wave)
+    bool empty;
+};
+
+__device__ __forceinline__ TcUnit tc_decode(const TensorArgs& a, int64_t u)
+{
+    TcUnit U;
+    int lo = a.slot_begin, hi = a.slot_end - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.unit_start[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    const int slot = lo;
+    U.c = a.order[slot];
+    U.n = a.cp[U.c].n;
+    U.nmt = tc_mtiles(U.n);
+    U.nkc = tc_kchunks(U.n);
+    U.wbase = a.wtile_start[slot] - a.wtile_base;
+    const int64_t chunk = u - a.unit_start[slot];
+    const int ft = 128 / a.n_max;
+    U.peak = 0;
+    U.peak_mult = 0;
+    U.empty = false;
+    if (a.stage == kStageFine) {
+        const int W = 2 * a.fine_half + 1;
+        const int upp = (W + ft - 1) / ft;
+        U.peak = (int)(chunk / upp);
+        const int sub = (int)(chunk - (int64_t)U.peak * upp);
+        U.empty = U.peak >= a.n_peaks[U.c];
+        U.peak_mult = U.empty ? 0 : (uint64_t)a.peaks[(int64_t)U.c * a.top_k + U.peak];
+        U.kfirst = -a.fine_half + (int64_t)sub * ft;
+        U.count = (int)min((int64_t)ft, (int64_t)a.fine_half - U.kfirst + 1);
+    } else {
+        U.kfirst = chunk * ft;
+        U.count = (int)min((int64_t)ft, a.n_freq - U.kfirst);
+    }
+    return U;
+}
+
+__device__ __forceinline__ uint32_t tc_phase_u32(const TensorArgs& a, const TcUnit& U, int64_t off, int i, int f)
+{
+    const uint64_t st = a.ph_step[off + i];
+    uint64_t ph = a.ph_base[off + i] + (uint64_t)(U.kfirst + f) * st;
+    if (a.stage == kStageFine) ph += U.peak_mult * a.ph_coarse[off + i];
+    return (uint32_t)(ph >> 32);
+}
+
+template <int NMAX>
+__global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + kTcStages * kTcA;
+    // producers' phase table of the current unit: (phase at the unit's first frequency, step)
+    ulonglong2* sPh = reinterpret_cast<ulonglong2*>(sB + kTcStages * kTcB);
+    __shared__ uint64_t bar_afull[kTcStages], bar_bfull[kTcStages], bar_empty[kTcStages];
+    __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_abort;
+    __shared__ float s_red[4][32];
+    __shared__ float s_acc[32];
+
+    constexpr int FT = 128 / NMAX;                    // frequencies per unit (256 columns)
+    constexpr int items = 8 * FT;                     // (j-octet, frequency) per stage
+    // Stages produced concurrently.  A group owns every use of its stages, so
+    // it never waits more than one barrier phase ahead; hence groups <= stages.
+    constexpr int groups = kTcProducers / items < kTcStages ? kTcProducers / items : kTcStages;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ft = FT;
+
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; s++) {
+            mbar_init(&bar_afull[s], 1);
+            mbar_init(&bar_bfull[s], items);
+            mbar_init(&bar_empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bar_tfull[b], 1);
+            mbar_init(&bar_tempty[b], 128);
+        }
+        mbar_init(&bar_drain, 1);
+        s_abort = 0;
+        fence_mbar_init();
+    }
+    if (tid < 32) s_acc[tid] = 0.f;
+    if (warp == 0) {
+        tmem_alloc(&s_taddr, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+
+    if (warp == 0) {
+        // ---------------- W' tile loader ----------------
+        if (lane == 0) {
+            uint32_t q = 0;
+            bool ok = true;
+            for (int64_t u = a.unit_begin + blockIdx.x; ok && u < a.unit_end; u += gridDim.x) {
+                const TcUnit U = tc_decode(a, u);
+                if (U.empty) continue;
+                for (int I = 0; ok && I < U.nmt; I++)
+                    for (int J = 2 * I; J < U.nkc; J++, q++) {
+                        const int s = q % kTcStages;
+                        if (!mbar_wait(&bar_empty[s], ((q / kTcStages) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
+                        mbar_arrive_expect_tx(&bar_afull[s], kTcA);
+                        const unsigned char* src = reinterpret_cast<const unsigned char*>(a.W16) +
+                                                   (U.wbase + tc_tile_index(I, J, U.nkc)) * (int64_t)kTcA;
+                        bulk_g2s(sA + s * kTcA, src, kTcA, &bar_afull[s]);
+                    }
+            }
+            if (!ok) {
+                // let copies already issued land before the CTA exits
+                for (uint32_t k = 0; k < kTcStages && q > 0; k++) {
+                    const uint32_t qq = q - 1 - k;
+                    mbar_wait(&bar_afull[qq % kTcStages], (qq / kTcStages) & 1, &s_abort, 1u << 20);
+                    if (qq == 0) break;
+                }
+                atomicOr(a.status, 2);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(128, kTcCols, a.bf16 != 0);
+            uint32_t q = 0, m = 0;
+            bool ok = true;
+            for (int64_t u = a.unit_begin + blockIdx.x; ok && u < a.unit_end; u += gridDim.x) {
+                const TcUnit U = tc_decode(a, u);
+                if (U.empty) continue;
+                for (int I = 0; ok && I < U.nmt; I++, m++) {
+                    const int b = m & 1;
+                    if (!mbar_wait(&bar_tempty[b], ((m >> 1) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t d = taddr + (uint32_t)(b * kTcCols);
+                    for (int J = 2 * I; J < U.nkc; J++, q++) {
+                        const int s = q % kTcStages;
+                        const uint32_t par = (q / kTcStages) & 1;
+                        if (!mbar_wait(&bar_afull[s], par, &s_abort, a.wait_limit) ||
+                            !mbar_wait(&bar_bfull[s], par, &s_abort, a.wait_limit)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(sA + s * kTcA), b0 = smem_u32(sB + s * kTcB);
+#pragma unroll
+                        for (int kk = 0; kk < 4; kk++)
+                            umma_f16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                                     (J > 2 * I || kk > 0) ? 1u : 0u);
+                        umma_commit(&bar_empty[s]);
+                    }
+                    if (ok) umma_commit(&bar_tfull[b]);
+                }
+            }
+            // every MMA issued has completed before TMEM can be released
+            umma_commit(&bar_drain);
+            mbar_wait(&bar_drain, 0, &s_abort, 1u << 22);
+            if (!ok) atomicOr(a.status, 2);
+        }
+    } else if (warp < 6) {
+        // ---------------- epilogue: 128 threads, one TMEM lane (W' row) each ----------------
+        const int lg = warp & 3;                      // TMEM lane group this warp may access
+        const int row = lg * 32 + lane;
+        const int ew = warp - 2;                      // epilogue warp index 0..3
+        uint32_t m = 0;
+        bool ok = true;
+        for (int64_t u = a.unit_begin + blockIdx.x; ok && u < a.unit_end; u += gridDim.x) {
+            const TcUnit U = tc_decode(a, u);
+            if (U.empty) continue;
+            const CurveParams& P = a.cp[U.c];
+            const int64_t off = P.off;
+            float an[NMAX];
+#pragma unroll
+            for (int q = 0; q < NMAX; q++) an[q] = a.coef[(int64_t)U.c * NMAX + q];
+            for (int I = 0; I < U.nmt; I++, m++) {
+                const int b = m & 1;
+                const int i = I * 128 + row;
+                const bool live = i < U.n;
+                // phase of this row at the unit's first frequency and its step (loaded before the wait)
+                uint64_t ph0 = 0, pstep = 0;
+                if (live) {
+                    pstep = a.ph_step[off + i];
+                    ph0 = a.ph_base[off + i] + (uint64_t)U.kfirst * pstep;
+                    if (a.stage == kStageFine) ph0 += U.peak_mult * a.ph_coarse[off + i];
+                }
+                mbar_wait(&bar_tfull[b], (m >> 1) & 1, &s_abort, a.wait_limit);
+                // agree on the outcome: every epilogue thread sees the abort flag after the barrier
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (s_abort) { ok = false; break; }
+                tc_fence_after();
+                float accf[FT];
+                const uint32_t tbase = taddr + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * kTcCols);
+                // columns: f * 2 NMAX + 2 (n - 1) + {0: cos, 1: sin}
+                float v[32];
+#pragma unroll
+                for (int f = 0; f < FT; f++) {
+                    float s1 = 0.f, c1 = 0.f;
+                    if (live) sincos2pi_turns((uint32_t)((ph0 + (uint64_t)f * pstep) >> 32), s1, c1);
+                    float cp2 = 1.f, sp2 = 0.f, cp1 = c1, sp1 = s1;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int n = 1; n <= NMAX; n++) {
+                        const int col = f * 2 * NMAX + 2 * (n - 1);
+                        if ((col & 31) == 0) tmem_ld32(tbase + col, v);
+                        acc = fmaf(an[n - 1], fmaf(v[col & 31], cp1, v[(col & 31) + 1] * sp1), acc);
+                        const float cn = fmaf(2.f * c1, cp1, -cp2), sn = fmaf(2.f * c1, sp1, -sp2);
+                        cp2 = cp1; sp2 = sp1;
+                        cp1 = cn; sp1 = sn;
+                    }
+                    accf[f] = live ? acc : 0.f;
+                }
+                tc_fence_before();
+                mbar_arrive(&bar_tempty[b]);
+                // sum over the 128 rows, fixed order
+#pragma unroll
+                for (int f = 0; f < FT; f++) {
+                    float x = accf[f];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    if (lane == 0) s_red[ew][f] = x;
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (ew == 0 && lane < ft) s_acc[lane] += ((s_red[0][lane] + s_red[1][lane]) + s_red[2][lane]) + s_red[3][lane];
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+            }
+            if (!ok) break;
+            // unit complete: normalise and emit
+            if (ew == 0) {
+                unsigned long long key = 0ull;
+                if (lane < U.count) {
+                    const float S = s_acc[lane];
+                    const float v = S * P.norm;
+                    const long long kk = U.kfirst + lane;
+                    if (a.stage == kStageFull) {
+                        if (a.out) a.out[(int64_t)U.c * a.out_ld + kk] = v;
+                        key = make_key(v, (uint32_t)kk);
+                    } else if (a.stage == kStageCoarse) {
+                        a.coarse_out[(int64_t)U.c * a.n_freq + kk] = v;
+                    } else {
+                        const double fpk = a.f_min + (double)U.peak_mult * a.coarse_df;
+                        const double fr = fpk + (double)kk * a.step;
+                        if (fr >= a.f_min && fr <= a.f_max)
+                            key = make_key(v, (uint32_t)(U.peak * (2 * a.fine_half + 1) + (kk + a.fine_half)));
+                    }
+                }
+                if (lane < 32) s_acc[lane] = 0.f;
+                if (a.stage != kStageCoarse) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+                        key = other > key ? other : key;
+                    }
+                    if (lane == 0 && key) atomicMax(a.best_key + U.c, key);
+                }
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+        if (!ok && ew == 0 && lane == 0) atomicOr(a.status, 2);
+    } else {
+        // ---------------- Z producers: 256 threads ----------------
+        const int pt = tid - 6 * 32;                  // 0..255
+        const int grp = pt / items;                   // stage group
+        const int it = pt - grp * items;
+        const int g = it & 7;                         // j-octet of the K chunk (fastest: conflict-free stores)
+        const int f = it >> 3;                        // frequency within the unit
+        const bool active = grp < groups;
+        uint32_t q = 0;
+        bool ok = true;
+        // After a timeout (ok == false) a producer keeps walking the units so that
+        // every producer executes the same named barriers; it skips all work.
+        for (int64_t u = a.unit_begin + blockIdx.x; u < a.unit_end; u += gridDim.x) {
+            const TcUnit U = tc_decode(a, u);
+            if (U.empty) continue;
+            const int64_t off = a.cp[U.c].off;
+            const bool tab = U.n <= kTcTablePoints;
+            if (tab) {
+                // every producer is done with the previous unit's table
+                asm volatile("bar.sync 2, 256;" ::: "memory");
+                for (int j = pt; ok && j < U.n; j += kTcProducers) {
+                    const uint64_t stp = a.ph_step[off + j];
+                    uint64_t ph0 = a.ph_base[off + j] + (uint64_t)U.kfirst * stp;
+                    if (a.stage == kStageFine) ph0 += U.peak_mult * a.ph_coarse[off + j];
+                    sPh[j] = make_ulonglong2(ph0, stp);
+                }
+                asm volatile("bar.sync 2, 256;" ::: "memory");
+            }
+            for (int I = 0; ok && I < U.nmt; I++)
+                for (int J = 2 * I; J < U.nkc; J++, q++) {
+                    if (!active || (int)(q % (uint32_t)groups) != grp) continue;
+                    const int s = q % kTcStages;
+                    const int j0 = J * 64 + g * 8;
+                    uint32_t pu[8];
+#pragma unroll
+                    for (int p = 0; p < 8; p++) {
+                        uint32_t v = 0u;
+                        if (j0 + p < U.n) {
+                            if (tab) {
+                                const ulonglong2 e = sPh[j0 + p];
+                                v = (uint32_t)((e.x + (uint64_t)f * e.y) >> 32);
+                            } else {
+                                v = tc_phase_u32(a, U, off, j0 + p, f);
+                            }
+                        }
+                        pu[p] = v;
+                    }
+                    if (!mbar_wait(&bar_empty[s], ((q / kTcStages) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
+                    float cc[8], ss[8], c1[8], cm[8], sm[8];
+#pragma unroll
+                    for (int p = 0; p < 8; p++) {
+                        float sv = 0.f, cv = 0.f;
+                        if (j0 + p < U.n) sincos2pi_turns(pu[p], sv, cv);
+                        c1[p] = cv;
+                        cc[p] = cv; ss[p] = sv;           // n = 1
+                        cm[p] = 1.f; sm[p] = 0.f;         // n = 0
+                    }
+                    unsigned char* Bs = sB + s * kTcB;
+#pragma unroll
+                    for (int n = 1; n <= NMAX; n++) {
+                        uint32_t pc[4], ps[4];
+#pragma unroll
+                        for (int p = 0; p < 8; p += 2) {
+                            pc[p >> 1] = (uint32_t)to16(cc[p], a.bf16) | ((uint32_t)to16(cc[p + 1], a.bf16) << 16);
+                            ps[p >> 1] = (uint32_t)to16(ss[p], a.bf16) | ((uint32_t)to16(ss[p + 1], a.bf16) << 16);
+                        }
+                        const int col = f * 2 * NMAX + 2 * (n - 1);
+                        *reinterpret_cast<uint4*>(Bs + sw128_offset(col, g * 8)) = make_uint4(pc[0], pc[1], pc[2], pc[3]);
+                        *reinterpret_cast<uint4*>(Bs + sw128_offset(col + 1, g * 8)) = make_uint4(ps[0], ps[1], ps[2], ps[3]);
+#pragma unroll
+                        for (int p = 0; p < 8; p++) {
+                            const float cn = fmaf(2.f * c1[p], cc[p], -cm[p]);
+                            const float sn = fmaf(2.f * c1[p], ss[p], -sm[p]);
+                            cm[p] = cc[p]; sm[p] = ss[p];
+                            cc[p] = cn; ss[p] = sn;
+                        }
+                    }
+                    fence_proxy_async_smem();
+                    mbar_arrive(&bar_bfull[s]);
+                }
+        }
+        if (!ok && it == 0) atomicOr(a.status, 2);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(taddr, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+size_t tensor_smem_bytes() { return (size_t)kTcStages * (kTcA + kTcB) + kTcTablePoints * 16 + 1024; }
+
+int tensor_tiles_of(int n) { return tc_tiles_of(n); }
+
+cudaError_t prepare_tensor_kernel(int n_max)
+{
+    const int b = (int)tensor_smem_bytes();
+    switch (n_max) {
+    case 4: return cudaFuncSetAttribute(k_pair_tensor<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 8: return cudaFuncSetAttribute(k_pair_tensor<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 16: return cudaFuncSetAttribute(k_pair_tensor<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 32: return cudaFuncSetAttribute(k_pair_tensor<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_build_w16(const BuildW16Args& a, cudaStream_t s)
+{
+    const int64_t tiles = a.tile_end - a.tile_begin;
+    if (tiles <= 0) return cudaSuccess;
+    k_build_w16<<<(unsigned)tiles, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max, float* coef, cudaStream_t s)
+{
+    k_harmonic_coef<<<(n_curves + 7) / 8, 256, 0, s>>>(cp, n_curves, n_max, coef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s)
+{
+    const size_t b = tensor_smem_bytes();
+    switch (a.n_max) {
+    case 4: k_pair_tensor<4><<<grid, kTcThreads, b, s>>>(a); break;
+    case 8: k_pair_tensor<8><<<grid, kTcThreads, b, s>>>(a); break;
+    case 16: k_pair_tensor<16><<<grid, kTcThreads, b, s>>>(a); break;
+    case 32: k_pair_tensor<32><<<grid, kTcThreads, b, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cpk

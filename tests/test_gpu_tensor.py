@@ -1,0 +1,147 @@
+"""Parity of the tensor-core form (Eq. (taylor) regrouped; tcgen05 GEMMs)
+against the FP64 oracle of Eq. (CKP).
+
+Bar: per curve max_k |nCKP_gpu - nCKP_oracle| / max_k |nCKP_oracle| <= 1e-3
+for FP16 operands with enough harmonics for the curve's sigma_t; the best
+index is accepted at the same tolerance (c16 reading).  BF16 operands carry
+8 mantissa bits, so their error is reported against a looser bound.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1412_1840_gb300 as cp  # noqa: E402
+
+TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def run(b, g, **kw):
+    with cp.Plan(b.times, b.mags, b.errs, b.offsets, cp.grid_from(g), **kw) as p:
+        out = torch.empty((b.n_curves, g.n_freq), dtype=torch.float32, device="cuda")
+        p.periodogram(out)
+        p.sync()
+        best = p.best_period()
+        st = p.curve_stats()
+    return out.cpu().numpy(), best, st
+
+
+def peak_err(gpu, ref, rows):
+    return np.array([np.max(np.abs(gpu[c] - ref[c])) / np.max(np.abs(ref[c])) for c in rows])
+
+
+def accept_best(best, ref, rows, tol):
+    for c in rows:
+        k = int(best["best_idx"][c])
+        vstar = ref[c].max()
+        assert ref[c, k] >= vstar - tol * abs(vstar), (c, k, int(np.argmax(ref[c])))
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    b = synth.ragged_batch(8, seed=21)
+    g = synth.Grid(0.002, 1e-4, 520)
+    ref = oracle.batch_nckp(b, np.full(b.n_curves, float(np.float32(0.45))), g.freqs())
+    return b, g, ref
+
+
+@pytest.mark.parametrize("n_max", [16, 32])
+def test_tensor_fp16_parity_ragged(ragged, n_max):
+    b, g, ref = ragged
+    out, best, _ = run(b, g, sigma_t=0.45, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_FP16, n_max=n_max)
+    rows = range(b.n_curves)
+    err = peak_err(out, ref, rows)
+    assert np.all(err <= TOL), err
+    accept_best(best, ref, rows, TOL)
+
+
+def test_tensor_truncation_converges_with_n_max(ragged):
+    """Too few harmonics for sigma_t = 0.45 (n_max = 4: tail 1.5e-2 of the
+    kernel peak) must show in the error; n_max = 8 and 16 approach the FP16
+    rounding floor."""
+    b, g, ref = ragged
+    errs = {}
+    for nm in (4, 8, 16):
+        out, _, _ = run(b, g, sigma_t=0.45, form=cp.CP_FORM_TENSOR, n_max=nm)
+        errs[nm] = peak_err(out, ref, range(b.n_curves)).max()
+    assert errs[4] > 2e-3 and errs[4] > errs[8] >= 0.5 * errs[16]
+    assert errs[16] <= TOL
+
+
+def test_tensor_bf16_error_bound(ragged):
+    b, g, ref = ragged
+    out, best, _ = run(b, g, sigma_t=0.45, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_BF16, n_max=16)
+    err = peak_err(out, ref, range(b.n_curves))
+    assert np.all(err <= 3e-2), err          # 8-bit mantissa: ~8x the FP16 error
+
+
+def test_tensor_edge_batch():
+    b = synth.edge_batch()
+    g = synth.Grid(0.005, 0.005, 600)
+    st = float(np.float32(0.3))
+    out, best, _ = run(b, g, sigma_t=0.3, form=cp.CP_FORM_TENSOR, n_max=16)
+    ref = oracle.batch_nckp(b, np.full(b.n_curves, st), g.freqs())
+    const = 3
+    assert np.all(out[const] == 0.0)
+    rows = [c for c in range(b.n_curves) if c != const]
+    err = peak_err(out, ref, rows)
+    assert np.all(err <= TOL), err
+    accept_best(best, ref, rows, TOL)
+
+
+def test_tensor_hierarchical_search():
+    b = synth.ragged_batch(6, seed=24, n_lo=100, n_hi=260, span=1200.0)
+    g = synth.Grid(0.01, 1e-4, 19901, hierarchical=True, coarse_df=4e-3, top_k=10, fine_df=1e-4,
+                   fine_halfwidth=4e-3)
+    with cp.Plan(b.times, b.mags, b.errs, b.offsets, cp.grid_from(g), sigma_t=0.35,
+                 form=cp.CP_FORM_TENSOR, n_max=16) as p:
+        best = p.best_period()
+    st = np.full(b.n_curves, float(np.float32(0.35)))
+    ref = oracle.batch_best(b, g, sigma_t_mode=1, sigma_t_per_curve=st)
+    for c in range(b.n_curves):
+        t, m, e = b.curve(c)
+        v = oracle.nckp(t, m.astype(np.float64), oracle.median(e.astype(np.float64)), st[c], [best["best_freq"][c]])[0]
+        vstar = ref["best_stat"][c]
+        assert v >= vstar - TOL * abs(vstar), (c, best["best_freq"][c], ref["best_freq"][c])
+        assert abs(best["best_stat"][c] - v) <= TOL * abs(vstar)
+
+
+def test_tensor_matches_direct_best_on_larger_batch():
+    b = synth.ragged_batch(64, seed=31)
+    g = synth.Grid(0.05, 1e-4, 1500)
+    _, bd, _ = run(b, g, sigma_t=0.4)
+    out, bt, _ = run(b, g, sigma_t=0.4, form=cp.CP_FORM_TENSOR, n_max=16)
+    assert np.mean(bd["best_idx"] == bt["best_idx"]) >= 0.95
+    rel = np.abs(bt["best_stat"] - bd["best_stat"]) / np.abs(bd["best_stat"])
+    assert np.median(rel) < 2e-4
+
+
+def test_bounded_waits_report_timeout_and_keep_context():
+    """With a one-poll wait limit every pipeline wait gives up: the kernel must
+    return CP_ETIMEOUT (not hang), and the context stays usable."""
+    b = synth.ragged_batch(4, seed=32, n_lo=300, n_hi=400)
+    g = synth.Grid(0.01, 1e-3, 64)
+    os.environ["CP_WAIT_LIMIT"] = "1"
+    try:
+        with cp.Plan(b.times, b.mags, b.errs, b.offsets, cp.grid_from(g), form=cp.CP_FORM_TENSOR) as p:
+            with pytest.raises(cp.CpError) as e:
+                p.best_period()
+        assert e.value.status == cp.CP_ETIMEOUT
+    finally:
+        del os.environ["CP_WAIT_LIMIT"]
+    _, ok, _ = run(b, g, form=cp.CP_FORM_TENSOR)
+    _, ref, _ = run(b, g)
+    assert np.mean(ok["best_idx"] == ref["best_idx"]) >= 0.75
+    torch.cuda.synchronize()
