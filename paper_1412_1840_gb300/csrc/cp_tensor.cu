@@ -75,6 +75,18 @@ __device__ __forceinline__ uint16_t to16(float v, bool bf)
     return bf ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
 }
 
+// Two floats -> one packed 16-bit pair (low = lo), one conversion instruction.
+template <bool BF>
+__device__ __forceinline__ uint32_t pack16x2(float lo, float hi)
+{
+    uint32_t r;
+    if (BF)
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    else
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 // ===========================================================================
 // k_build_w16: pre-swizzled 128 x 64 tiles of W' (one CTA per tile).
 // ===========================================================================
@@ -214,7 +226,7 @@ __device__ __forceinline__ uint32_t tc_phase_u32(const TensorArgs& a, const TcUn
     return (uint32_t)(ph >> 32);
 }
 
-template <int NMAX>
+template <int NMAX, bool BF>
 __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -293,7 +305,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_f16(128, kTcCols, a.bf16 != 0);
+            constexpr uint32_t idesc = idesc_f16(128, kTcCols, BF);
             uint32_t q = 0, m = 0;
             bool ok = true;
             for (int64_t u = a.unit_begin + blockIdx.x; ok && u < a.unit_end; u += gridDim.x) {
@@ -487,8 +499,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                         uint32_t pc[4], ps[4];
 #pragma unroll
                         for (int p = 0; p < 8; p += 2) {
-                            pc[p >> 1] = (uint32_t)to16(cc[p], a.bf16) | ((uint32_t)to16(cc[p + 1], a.bf16) << 16);
-                            ps[p >> 1] = (uint32_t)to16(ss[p], a.bf16) | ((uint32_t)to16(ss[p + 1], a.bf16) << 16);
+                            pc[p >> 1] = pack16x2<BF>(cc[p], cc[p + 1]);
+                            ps[p >> 1] = pack16x2<BF>(ss[p], ss[p + 1]);
                         }
                         const int col = f * 2 * NMAX + 2 * (n - 1);
                         *reinterpret_cast<uint4*>(Bs + sw128_offset(col, g * 8)) = make_uint4(pc[0], pc[1], pc[2], pc[3]);
@@ -521,16 +533,23 @@ size_t tensor_smem_bytes() { return (size_t)kTcStages * (kTcA + kTcB) + kTcTable
 
 int tensor_tiles_of(int n) { return tc_tiles_of(n); }
 
+template <int NMAX, bool BF>
+static cudaError_t set_tensor_smem()
+{
+    return cudaFuncSetAttribute(k_pair_tensor<NMAX, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tensor_smem_bytes());
+}
+
 cudaError_t prepare_tensor_kernel(int n_max)
 {
-    const int b = (int)tensor_smem_bytes();
+    cudaError_t e = cudaErrorInvalidValue;
     switch (n_max) {
-    case 4: return cudaFuncSetAttribute(k_pair_tensor<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    case 8: return cudaFuncSetAttribute(k_pair_tensor<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    case 16: return cudaFuncSetAttribute(k_pair_tensor<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    case 32: return cudaFuncSetAttribute(k_pair_tensor<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    case 4: e = set_tensor_smem<4, false>(); if (e == cudaSuccess) e = set_tensor_smem<4, true>(); break;
+    case 8: e = set_tensor_smem<8, false>(); if (e == cudaSuccess) e = set_tensor_smem<8, true>(); break;
+    case 16: e = set_tensor_smem<16, false>(); if (e == cudaSuccess) e = set_tensor_smem<16, true>(); break;
+    case 32: e = set_tensor_smem<32, false>(); if (e == cudaSuccess) e = set_tensor_smem<32, true>(); break;
     }
-    return cudaErrorInvalidValue;
+    return e;
 }
 
 cudaError_t launch_build_w16(const BuildW16Args& a, cudaStream_t s)
@@ -550,13 +569,20 @@ cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max,
 cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s)
 {
     const size_t b = tensor_smem_bytes();
+    const bool bf = a.bf16 != 0;
+#define CP_TC_LAUNCH(NM)                                                        \
+    case NM:                                                                    \
+        if (bf) k_pair_tensor<NM, true><<<grid, kTcThreads, b, s>>>(a);         \
+        else k_pair_tensor<NM, false><<<grid, kTcThreads, b, s>>>(a);           \
+        break;
     switch (a.n_max) {
-    case 4: k_pair_tensor<4><<<grid, kTcThreads, b, s>>>(a); break;
-    case 8: k_pair_tensor<8><<<grid, kTcThreads, b, s>>>(a); break;
-    case 16: k_pair_tensor<16><<<grid, kTcThreads, b, s>>>(a); break;
-    case 32: k_pair_tensor<32><<<grid, kTcThreads, b, s>>>(a); break;
+        CP_TC_LAUNCH(4)
+        CP_TC_LAUNCH(8)
+        CP_TC_LAUNCH(16)
+        CP_TC_LAUNCH(32)
     default: return cudaErrorInvalidValue;
     }
+#undef CP_TC_LAUNCH
     return cudaGetLastError();
 }
 
