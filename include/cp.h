@@ -88,8 +88,11 @@ typedef struct {
     float alpha;                     /* error-bar correction factor of Eq. (pSNR), >0   */
     int32_t form;                    /* CP_FORM_*                                       */
     int32_t dtype;                   /* CP_DTYPE_* (tensor form only)                   */
-    int32_t n_max;                   /* harmonics of the tensor form; 0 = per curve,    */
-                                     /* smallest n with truncation tail <= 1e-4         */
+    int32_t n_max;                   /* harmonics of the tensor form (4, 8, 16, 32); 0 = */
+                                     /* per curve: the smallest of 8, 16, 32 whose      */
+                                     /* truncation tail is <= 1e-4 of the kernel peak   */
+                                     /* for the curve's sigma_t at plan time; curves    */
+                                     /* that need more run in the direct form           */
     int32_t input_memory;            /* CP_MEM_HOST or CP_MEM_DEVICE                    */
     int32_t use_graph;               /* capture cp_best_period's step in a CUDA graph   */
     int32_t device;                  /* CUDA device ordinal                             */
@@ -172,6 +175,8 @@ typedef struct {
     float last_step_ms;           /* device time of the whole last cp_best_period       */
     int32_t n_sm;                 /* SMs of the plan's device                           */
     int32_t max_n;                /* largest N in the batch                             */
+    int64_t class_curves[5];      /* curves per evaluation class: direct form, then the */
+                                  /* tensor form with 4, 8, 16, 32 harmonics            */
 } cp_plan_info;
 
 cp_status cp_get_plan_info(cp_plan_t plan, cp_plan_info *info);

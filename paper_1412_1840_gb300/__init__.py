@@ -51,7 +51,7 @@ class cp_plan_info(ctypes.Structure):
     _fields_ = [("n_curves", ctypes.c_int64), ("n_points", ctypes.c_int64), ("pair_freq_full", ctypes.c_double),
                 ("pair_freq_search", ctypes.c_double), ("launches_per_search", ctypes.c_int64),
                 ("last_pair_kernel_ms", ctypes.c_float), ("last_step_ms", ctypes.c_float),
-                ("n_sm", ctypes.c_int32), ("max_n", ctypes.c_int32)]
+                ("n_sm", ctypes.c_int32), ("max_n", ctypes.c_int32), ("class_curves", ctypes.c_int64 * 5)]
 
 
 _lock = threading.Lock()
@@ -232,7 +232,9 @@ class Plan:
     def info(self) -> dict:
         i = cp_plan_info()
         _check(_load().cp_get_plan_info(self.handle, ctypes.byref(i)), "cp_get_plan_info")
-        return {k: getattr(i, k) for k, _ in cp_plan_info._fields_}
+        d = {k: getattr(i, k) for k, _ in cp_plan_info._fields_}
+        d["class_curves"] = list(i.class_curves)
+        return d
 
     def close(self):
         if getattr(self, "handle", None):

@@ -68,6 +68,7 @@ static cp_status finish(cp_status st, const char* where)
 struct Wave {
     int slot_begin, slot_end;
     int64_t tile_begin, tile_end;
+    int cls;              // 0: direct form; else the tensor form with this many harmonics
 };
 
 struct PairLaunch {
@@ -100,6 +101,8 @@ struct cp_plan_s {
 
     std::vector<int32_t> order;          // slot -> curve
     std::vector<int32_t> fc;             // per curve
+    std::vector<int32_t> cls;            // per curve: 0 direct, else tensor harmonics
+    int64_t class_count[5] = {0, 0, 0, 0, 0};   // curves per class {direct, 4, 8, 16, 32}
     std::vector<int64_t> unit_full, unit_coarse, unit_fine, wtile;
     std::vector<Wave> waves;
     size_t pair_smem = 0;
@@ -162,6 +165,95 @@ inline unsigned long long* status_word(cp_plan_t p) { return p->d_u64; }
 inline unsigned long long* best_keys(cp_plan_t p) { return p->d_u64 + 1; }
 inline unsigned long long* queue_word(cp_plan_t p, int i) { return p->d_u64 + 1 + p->n_curves + i; }
 
+constexpr int kCoefStride = 32;   // a_1..a_32 stored per curve (largest class)
+
+int class_rank(int cls)
+{
+    switch (cls) {
+    case 4: return 1;
+    case 8: return 2;
+    case 16: return 3;
+    case 32: return 4;
+    }
+    return 0;   // direct form
+}
+
+// Truncation tail 1 - (a_0 + ... + a_n) of the periodic kernel's harmonic
+// series, relative to its peak value 1.
+double harmonic_tail(double sigma_t, int n)
+{
+    double a[33];
+    if (cp_bessel_coefficients(sigma_t, n, a) != CP_OK) return 1.0;
+    double s = 0.0;
+    for (int k = 0; k <= n; k++) s += a[k];
+    return 1.0 - s;
+}
+
+// Smallest harmonic count of the tensor form whose truncation tail stays
+// below 1e-4 of the kernel peak; 0 (direct form) when even 32 harmonics do
+// not reach it (sigma_t below about 0.13).  The tail falls as sigma_t grows,
+// so each class is a threshold on sigma_t, found once by bisection.
+int harmonics_for(float sigma_t)
+{
+    static const std::vector<double> thr = [] {
+        std::vector<double> t;
+        for (int n : {8, 16, 32}) {
+            double lo = 0.02, hi = 4.0;
+            for (int it = 0; it < 40; it++) {
+                const double mid = 0.5 * (lo + hi);
+                if (harmonic_tail(mid, n) <= 1e-4) hi = mid; else lo = mid;
+            }
+            t.push_back(hi);
+        }
+        return t;
+    }();
+    const int cls[3] = {8, 16, 32};
+    for (int k = 0; k < 3; k++)
+        if ((double)sigma_t >= thr[k]) return cls[k];
+    return 0;
+}
+
+double median_of_sorted(const float* v, int n)
+{
+    return (n & 1) ? (double)v[n / 2] : 0.5 * ((double)v[n / 2 - 1] + (double)v[n / 2]);
+}
+
+// sigma_t of every curve as the plan sees it at creation time (to choose the
+// tensor form's harmonic count per curve).  The rule mode reads the current
+// magnitudes (copied from the device once when they live there).
+cp_status plan_sigma_t(cp_plan_t p, const cp_options& opt, std::vector<float>& st)
+{
+    const int64_t nc = p->n_curves;
+    if (opt.sigma_t_mode == CP_SIGMA_T_FIXED) {
+        std::fill(st.begin(), st.end(), opt.sigma_t);
+        return CP_OK;
+    }
+    if (opt.sigma_t_mode == CP_SIGMA_T_PER_CURVE) {
+        for (int64_t c = 0; c < nc; c++) st[c] = opt.sigma_t_per_curve[c];
+        return CP_OK;
+    }
+    std::vector<float> mags;
+    const float* m = p->mags;
+    if (!p->host_inputs) {
+        mags.resize((size_t)p->n_points);
+        CP_CUDA(cudaMemcpy(mags.data(), p->mags, (size_t)p->n_points * sizeof(float), cudaMemcpyDeviceToHost));
+        m = mags.data();
+    }
+    std::vector<float> y;
+    for (int64_t c = 0; c < nc; c++) {
+        const int64_t o = p->offsets[c];
+        const int n = (int)(p->offsets[c + 1] - o);
+        y.assign(m + o, m + o + n);
+        std::sort(y.begin(), y.end());
+        const int h = n / 2;
+        const double q2 = median_of_sorted(y.data(), n);
+        const double lq = median_of_sorted(y.data(), h), uq = median_of_sorted(y.data() + (n - h), h);
+        const double sk = (uq == lq) ? 0.0 : (uq + lq - 2.0 * q2) / (uq - lq);
+        st[c] = std::isfinite(sk) ? (float)(0.1 + 0.5 * std::exp(-12.0 * sk * sk)) : 0.1f;
+    }
+    return CP_OK;
+}
+
 // Events recorded during capture must be external nodes to stay timeable;
 // outside capture the flag is not allowed.
 unsigned rec_flags(cp_plan_t p) { return p->capturing ? cudaEventRecordExternal : cudaEventRecordDefault; }
@@ -223,7 +315,7 @@ cp_status enqueue_stats(cp_plan_t p, cudaStream_t s)
     a.np2max = p->np2max;
     a.status = reinterpret_cast<int*>(status_word(p));
     CP_CUDA(launch_stats(a, (int)p->n_curves, s));
-    if (p->tensor) CP_CUDA(launch_harmonic_coef(p->d_cp, (int)p->n_curves, p->n_max, p->d_coef, s));
+    if (p->tensor) CP_CUDA(launch_harmonic_coef(p->d_cp, (int)p->n_curves, kCoefStride, p->d_coef, s));
     return CP_OK;
 }
 
@@ -282,7 +374,7 @@ PairArgs pair_args(cp_plan_t p, int stage, int w, float* out)
 cp_status enqueue_wave_w(cp_plan_t p, int w, cudaStream_t s)
 {
     const Wave& wv = p->waves[w];
-    if (p->tensor) {
+    if (wv.cls != 0) {
         BuildW16Args b{};
         b.cp = p->d_cp;
         b.order = p->d_order;
@@ -320,6 +412,7 @@ TensorArgs tensor_args(const PairArgs& d, cp_plan_t p)
     t.wtile_start = d.wtile_start;
     t.W16 = p->d_W16;
     t.coef = p->d_coef;
+    t.coef_stride = kCoefStride;
     t.ph_base = d.ph_base;
     t.ph_step = d.ph_step;
     t.ph_coarse = d.ph_coarse;
@@ -353,10 +446,13 @@ cp_status enqueue_pair(cp_plan_t p, int stage, int w, float* out, cudaStream_t s
 {
     const PairArgs a = pair_args(p, stage, w, out);
     if (ev_idx) CP_CUDA(cudaEventRecordWithFlags(p->ev_pair[2 * (*ev_idx)], s, rec_flags(p)));
-    if (p->tensor)
-        CP_CUDA(launch_pair_tensor(tensor_args(a, p), p->pair_grid, s));
-    else
+    if (p->waves[w].cls != 0) {
+        TensorArgs t = tensor_args(a, p);
+        t.n_max = p->waves[w].cls;
+        CP_CUDA(launch_pair_tensor(t, p->n_sm, s));
+    } else {
         CP_CUDA(launch_pair_direct(a, p->pair_grid, p->pair_smem, s));
+    }
     if (ev_idx) {
         CP_CUDA(cudaEventRecordWithFlags(p->ev_pair[2 * (*ev_idx) + 1], s, rec_flags(p)));
         (*ev_idx)++;
@@ -527,9 +623,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     if (opt.form == CP_FORM_TENSOR) {
         if (opt.dtype != CP_DTYPE_FP16 && opt.dtype != CP_DTYPE_BF16)
             return fail(CP_EINVAL, "cp_plan: dtype must be CP_DTYPE_FP16 or CP_DTYPE_BF16");
-        if (opt.n_max == 0) opt.n_max = 16;
-        if (opt.n_max != 4 && opt.n_max != 8 && opt.n_max != 16 && opt.n_max != 32)
-            return fail(CP_EINVAL, "cp_plan: n_max must be 0, 4, 8, 16 or 32");
+        if (opt.n_max != 0 && opt.n_max != 4 && opt.n_max != 8 && opt.n_max != 16 && opt.n_max != 32)
+            return fail(CP_EINVAL, "cp_plan: n_max must be 0 (per curve), 4, 8, 16 or 32");
         p->tensor = true;
         p->n_max = opt.n_max;
         // test hook: shorter bounded waits, to exercise the timeout path
@@ -621,10 +716,26 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         }
     }
 
-    // schedule: slots sorted by N descending (stable)
+    // per-curve evaluation class: 0 = direct form, else tensor form with cls harmonics
+    p->cls.assign(n_curves, 0);
+    if (p->tensor) {
+        if (opt.n_max != 0) {
+            std::fill(p->cls.begin(), p->cls.end(), opt.n_max);
+        } else {
+            std::vector<float> st((size_t)n_curves);
+            cp_status s2 = plan_sigma_t(p, opt, st);
+            if (s2 != CP_OK) return s2;
+            for (int64_t c = 0; c < n_curves; c++) p->cls[c] = harmonics_for(st[c]);
+        }
+    }
+    for (int64_t c = 0; c < n_curves; c++) p->class_count[class_rank(p->cls[c])]++;
+
+    // schedule: slots grouped by class, N descending within a class (stable)
     p->order.resize(n_curves);
     std::iota(p->order.begin(), p->order.end(), 0);
     std::stable_sort(p->order.begin(), p->order.end(), [&](int32_t a, int32_t b) {
+        const int ra = class_rank(p->cls[a]), rb = class_rank(p->cls[b]);
+        if (ra != rb) return ra < rb;
         return (offsets[a + 1] - offsets[a]) > (offsets[b + 1] - offsets[b]);
     });
     p->unit_full.assign(n_curves + 1, 0);
@@ -636,7 +747,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     for (int64_t s = 0; s < n_curves; s++) {
         const int c = p->order[s];
         const int n = (int)(offsets[c + 1] - offsets[c]);
-        const int f = p->tensor ? 128 / p->n_max : p->fc[c];
+        const int f = p->cls[c] ? 128 / p->cls[c] : p->fc[c];
         const double pairs = 0.5 * (double)n * (double)(n - 1);
         p->unit_full[s + 1] = p->unit_full[s] + (g.n_freq + f - 1) / f;
         if (g.hierarchical) {
@@ -647,34 +758,42 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             pf_search += pairs * (double)g.n_freq;
         }
         pf_full += pairs * (double)g.n_freq;
-        p->wtile[s + 1] = p->wtile[s] + (p->tensor ? tensor_tiles_of(n) : tiles_of(n));
+        // tile counts in the unit of the curve's form (a wave never mixes forms)
+        p->wtile[s + 1] = p->wtile[s] + (p->cls[c] ? tensor_tiles_of(n) : tiles_of(n));
         const size_t npad = (size_t)((n + kTile - 1) / kTile * kTile);
-        smem = std::max(smem, npad * (size_t)p->fc[c] * 12);   // direct-form trig table
+        if (!p->cls[c]) smem = std::max(smem, npad * (size_t)p->fc[c] * 12);   // direct-form trig table
     }
     p->pf_full = pf_full;
     p->pf_search = pf_search;
-    p->pair_smem = smem;
+    p->pair_smem = std::max<size_t>(smem, 1024);
 
-    // waves bounded by the W buffer budget
+    // waves: contiguous slots of one class, bounded by the W buffer budget
     size_t free_b = 0, total_b = 0;
     CP_CUDA(cudaMemGetInfo(&free_b, &total_b));
     size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 3);
     if (const char* env = std::getenv("CP_W_BUDGET_KB")) budget = (size_t)std::atoll(env) << 10;
-    const size_t tile_bytes = p->tensor ? (size_t)128 * 64 * 2 : kTileFloats * sizeof(float);
-    const int64_t tile_budget = std::max<int64_t>(1, (int64_t)(budget / tile_bytes));
-    int64_t max_wave_tiles = 0;
+    const size_t tile16_bytes = (size_t)128 * 64 * 2, tile32_bytes = kTileFloats * sizeof(float);
+    int64_t max_tiles32 = 0, max_tiles16 = 0;
     {
+        auto close_wave = [&](int sb, int se) {
+            const int cl = p->cls[p->order[sb]];
+            const int64_t nt = p->wtile[se] - p->wtile[sb];
+            p->waves.push_back({sb, se, p->wtile[sb], p->wtile[se], cl});
+            if (cl) max_tiles16 = std::max(max_tiles16, nt); else max_tiles32 = std::max(max_tiles32, nt);
+        };
         int sb = 0;
         for (int s = 0; s < (int)n_curves; s++) {
-            const int64_t t_end = p->wtile[s + 1];
-            if (t_end - p->wtile[sb] > tile_budget && s > sb) {
-                p->waves.push_back({sb, s, p->wtile[sb], p->wtile[s]});
-                max_wave_tiles = std::max(max_wave_tiles, p->wtile[s] - p->wtile[sb]);
+            const int cl = p->cls[p->order[s]];
+            const int64_t tile_budget =
+                std::max<int64_t>(1, (int64_t)(budget / (cl ? tile16_bytes : tile32_bytes)));
+            const bool new_class = s > sb && cl != p->cls[p->order[sb]];
+            const bool over = s > sb && p->wtile[s + 1] - p->wtile[sb] > tile_budget;
+            if (new_class || over) {
+                close_wave(sb, s);
                 sb = s;
             }
         }
-        p->waves.push_back({sb, (int)n_curves, p->wtile[sb], p->wtile[n_curves]});
-        max_wave_tiles = std::max(max_wave_tiles, p->wtile[n_curves] - p->wtile[sb]);
+        close_wave(sb, (int)n_curves);
     }
 
     // device allocation (one block)
@@ -699,9 +818,9 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         {(void**)&p->d_unit_coarse, (nc + 1) * sizeof(int64_t)},
         {(void**)&p->d_unit_fine, (nc + 1) * sizeof(int64_t)},
         {(void**)&p->d_wtile, (nc + 1) * sizeof(int64_t)},
-        {(void**)&p->d_W, p->tensor ? 0 : (size_t)max_wave_tiles * kTileFloats * sizeof(float)},
-        {(void**)&p->d_W16, p->tensor ? (size_t)max_wave_tiles * tile_bytes : 0},
-        {(void**)&p->d_coef, p->tensor ? (size_t)nc * p->n_max * sizeof(float) : 0},
+        {(void**)&p->d_W, (size_t)max_tiles32 * tile32_bytes},
+        {(void**)&p->d_W16, (size_t)max_tiles16 * tile16_bytes},
+        {(void**)&p->d_coef, p->tensor ? (size_t)nc * kCoefStride * sizeof(float) : 0},
         {(void**)&p->d_coarse, hier ? (size_t)nc * p->kc * sizeof(float) : 0},
         {(void**)&p->d_peaks, hier ? (size_t)nc * g.top_k * sizeof(int32_t) : 0},
         {(void**)&p->d_npeaks, hier ? nc * sizeof(int32_t) : 0},
@@ -771,10 +890,9 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
 
     // launch geometry of the persistent pair kernel
     CP_CUDA(prepare_kernels(p->np2max, p->pair_smem));
-    if (p->tensor) {
-        CP_CUDA(prepare_tensor_kernel(p->n_max));
-        p->pair_grid = p->n_sm;    // one CTA per SM: 193 KB of shared memory and all 512 TMEM columns
-    } else {
+    for (int nm : {4, 8, 16, 32})
+        if (p->class_count[class_rank(nm)]) CP_CUDA(prepare_tensor_kernel(nm));   // one CTA per SM
+    {
         int occ = 1;
         CP_CUDA(pair_direct_occupancy(&occ, p->pair_smem));
         p->pair_grid = p->n_sm * std::max(occ, 1);
@@ -935,6 +1053,7 @@ cp_status cp_get_plan_info(cp_plan_t p, cp_plan_info* info)
     info->last_step_ms = p->last_step_ms;
     info->n_sm = p->n_sm;
     info->max_n = p->max_n;
+    for (int k = 0; k < 5; k++) info->class_curves[k] = p->class_count[k];
     return CP_OK;
 }
 

@@ -164,7 +164,8 @@ struct TensorArgs {
     const int64_t* unit_start;
     const int64_t* wtile_start;
     const void* W16;
-    const float* coef;            // [n_curves * n_max] a_1 .. a_nmax
+    const float* coef;            // [n_curves * coef_stride] a_1 .. a_nmax
+    int32_t coef_stride;
     const uint64_t* ph_base;
     const uint64_t* ph_step;
     const uint64_t* ph_coarse;

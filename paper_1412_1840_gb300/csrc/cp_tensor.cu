@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
             const int64_t off = P.off;
             float an[NMAX];
 #pragma unroll
-            for (int q = 0; q < NMAX; q++) an[q] = a.coef[(int64_t)U.c * NMAX + q];
+            for (int q = 0; q < NMAX; q++) an[q] = a.coef[(int64_t)U.c * a.coef_stride + q];
             for (int I = 0; I < U.nmt; I++, m++) {
                 const int b = m & 1;
                 const int i = I * 128 + row;

@@ -145,3 +145,25 @@ def test_bounded_waits_report_timeout_and_keep_context():
     _, ref, _ = run(b, g)
     assert np.mean(ok["best_idx"] == ref["best_idx"]) >= 0.75
     torch.cuda.synchronize()
+
+
+def test_tensor_auto_harmonics_per_curve():
+    """n_max = 0 picks per curve the smallest of 8/16/32 harmonics whose
+    truncation tail is <= 1e-4; curves with sigma_t too small for 32 run in the
+    direct form.  Every curve must meet the tensor tolerance."""
+    b = synth.ragged_batch(10, seed=33, n_lo=150, n_hi=600)
+    st = np.array([0.1, 0.11, 0.13, 0.15, 0.2, 0.25, 0.3, 0.45, 0.55, 0.6], np.float32)
+    g = synth.Grid(0.01, 2e-4, 700)
+    with cp.Plan(b.times, b.mags, b.errs, b.offsets, cp.grid_from(g), sigma_t_per_curve=st,
+                 form=cp.CP_FORM_TENSOR, n_max=0) as p:
+        out = torch.empty((b.n_curves, g.n_freq), dtype=torch.float32, device="cuda")
+        p.periodogram(out)
+        p.sync()
+        best = p.best_period()
+        info = p.info()
+    out = out.cpu().numpy()
+    assert info["class_curves"] == [2, 0, 2, 3, 3]       # direct, 4, 8, 16, 32 harmonics
+    ref = oracle.batch_nckp(b, st.astype(np.float64), g.freqs())
+    err = peak_err(out, ref, range(b.n_curves))
+    assert np.all(err <= TOL), err
+    accept_best(best, ref, range(b.n_curves), TOL)
