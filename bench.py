@@ -40,6 +40,18 @@ import synth  # noqa: E402
 MUFU_EX2_PER_CLK_SM = 32      # measured sm_103a SFU ex2 rate (ex2 probe, 152 SMs)
 
 
+def measured_peaks():
+    """Measured peaks if present, else the profiling recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -49,7 +61,8 @@ def parse():
     ap.add_argument("--workload", default="ragged", choices=["ragged", "hierarchical", "single", "small"])
     ap.add_argument("--n-curves", type=int, default=None)
     ap.add_argument("--form", default="direct", choices=["direct", "tensor"])
-    ap.add_argument("--n-max", type=int, default=16, help="harmonics of the tensor form")
+    ap.add_argument("--n-max", type=int, default=0, help="tensor-form harmonics (0: per curve)")
+    ap.add_argument("--no-tensor", action="store_true", help="skip the tensor-form measurement")
     ap.add_argument("--dtype", default="fp16", choices=["fp16", "bf16"], help="tensor-form operand type")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -272,6 +285,55 @@ def main():
         e2e = {"value": world * n * e_steps / e_s, "unit": "lightcurves/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": e_steps}
 
+    # ---- tensor-core form on the same resident batch ---------------------
+    tensor = None
+    if not args.no_tensor and args.form == "direct":
+        tkw2 = dict(n_max=args.n_max, dtype=cp.CP_DTYPE_BF16 if args.dtype == "bf16" else cp.CP_DTYPE_FP16)
+        tplan = cp.Plan(td, md, ed, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=cp.CP_FORM_TENSOR,
+                        device=local, stream=stream.cuda_stream, **tkw2)
+        tidx = np.empty(n, np.int64); tbf = np.empty(n, np.float64); tbs = np.empty(n, np.float32)
+        tper = np.empty(n, np.uint8); tps = np.empty(n, np.float32)
+        for _ in range(max(1, min(args.warmup, 2))):
+            tplan.best_period_into(tidx, tbf, tbs, tper, tps)
+        t_steps = max(1, min(args.steps, 2))
+        te0 = [torch.cuda.Event(enable_timing=True) for _ in range(t_steps)]
+        te1 = [torch.cuda.Event(enable_timing=True) for _ in range(t_steps)]
+        tk_ms = []
+        barrier()
+        for k in range(t_steps):
+            flush.fill_(k & 0xff)
+            te0[k].record(stream)
+            tplan.best_period_into(tidx, tbf, tbs, tper, tps)
+            te1[k].record(stream)
+            ti = tplan.info()
+            tk_ms.append(ti["last_tensor_kernel_ms"])
+        barrier()
+        t_total = sum(te0[k].elapsed_time(te1[k]) for k in range(t_steps)) / 1e3
+        if dist is not None:
+            t = torch.tensor([t_total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_total = float(t.item())
+        tplan.close()
+        peaks = measured_peaks()
+        tflops = ti["tensor_flops_search"] / (np.mean(tk_ms) / 1e3) / 1e12
+        rel = np.abs(tbs.astype(np.float64) - bs) / np.maximum(np.abs(bs.astype(np.float64)), 1e-30)
+        tensor = {
+            "value": world * n * t_steps / t_total, "unit": "lightcurves/s",
+            "ms_per_step": t_total * 1e3 / t_steps, "steps": t_steps,
+            "dtype": args.dtype, "n_max": "per curve (8/16/32 by truncation tail <= 1e-4)" if args.n_max == 0
+            else args.n_max,
+            "class_curves": dict(zip(["direct", "n4", "n8", "n16", "n32"], ti["class_curves"])),
+            "best_idx_agreement_vs_direct": float(np.mean(tidx == idx)),
+            "best_stat_max_rel_diff_vs_direct": float(rel.max()),
+            "roofline": {"bound": "tensor", "achieved": tflops,
+                         "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                         "frac": tflops / peaks["bf16_tflops_sustained"], "traffic": None,
+                         "kernel": "k_pair_tensor", "flops_basis": "2 N^2 n_max per curve-frequency (upper block "
+                         "triangle of the 4 N^2 n_max dense GEMM)",
+                         "peak_basis": "bf16 dense sustained, %s (fp16 has the same nominal rate)" % peaks["source"],
+                         "avg_launch_ms": float(np.mean(tk_ms))},
+        }
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -284,7 +346,8 @@ def main():
     line = {
         "metric": "lightcurves/s", "value": value, "unit": "lightcurves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.form == "direct" else args.dtype,
         "data": "synthetic",
         "config": {"workload": name, "form": args.form, "sigma_t": "Bowley-skewness rule",
                    "curves_per_gpu": n, "l2": "flushed between steps (256 MB write)",
@@ -298,6 +361,15 @@ def main():
                      % info["n_sm"], "avg_launch_ms": float(np.mean(pair_ms))},
         "clocks": clocks,
     }
+    if args.form == "tensor":
+        peaks = measured_peaks()
+        tflops = info["tensor_flops_search"] / (info["last_tensor_kernel_ms"] / 1e3) / 1e12
+        line["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": peaks["bf16_tflops_sustained"],
+                            "unit": "TFLOP/s", "frac": tflops / peaks["bf16_tflops_sustained"], "traffic": None,
+                            "kernel": "k_pair_tensor", "peak_basis": "bf16 dense sustained, " + peaks["source"],
+                            "avg_launch_ms": float(info["last_tensor_kernel_ms"])}
+    if tensor is not None:
+        line["tensor"] = tensor
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(b, g)
         line["cpu_baseline"].pop("seconds", None)

@@ -177,6 +177,12 @@ typedef struct {
     int32_t max_n;                /* largest N in the batch                             */
     int64_t class_curves[5];      /* curves per evaluation class: direct form, then the */
                                   /* tensor form with 4, 8, 16, 32 harmonics            */
+    float last_tensor_kernel_ms;  /* device time of the tensor-form launches, last call */
+    float last_direct_kernel_ms;  /* device time of the direct-form launches, last call */
+    double tensor_flops_search;   /* tensor-form GEMM flops of one cp_best_period:      */
+                                  /* 2 N^2 n_max per curve and frequency (the upper     */
+                                  /* block triangle of the 4 N^2 n_max dense product)   */
+    double direct_pair_freq_search; /* pair-frequency evaluations of the direct curves  */
 } cp_plan_info;
 
 cp_status cp_get_plan_info(cp_plan_t plan, cp_plan_info *info);

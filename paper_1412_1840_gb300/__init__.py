@@ -51,7 +51,9 @@ class cp_plan_info(ctypes.Structure):
     _fields_ = [("n_curves", ctypes.c_int64), ("n_points", ctypes.c_int64), ("pair_freq_full", ctypes.c_double),
                 ("pair_freq_search", ctypes.c_double), ("launches_per_search", ctypes.c_int64),
                 ("last_pair_kernel_ms", ctypes.c_float), ("last_step_ms", ctypes.c_float),
-                ("n_sm", ctypes.c_int32), ("max_n", ctypes.c_int32), ("class_curves", ctypes.c_int64 * 5)]
+                ("n_sm", ctypes.c_int32), ("max_n", ctypes.c_int32), ("class_curves", ctypes.c_int64 * 5),
+                ("last_tensor_kernel_ms", ctypes.c_float), ("last_direct_kernel_ms", ctypes.c_float),
+                ("tensor_flops_search", ctypes.c_double), ("direct_pair_freq_search", ctypes.c_double)]
 
 
 _lock = threading.Lock()

@@ -152,7 +152,9 @@ struct cp_plan_s {
     bool graph_ready = false;
     std::vector<cudaEvent_t> ev_pair;      // 2 per pair launch of a search
     cudaEvent_t ev_step0 = nullptr, ev_step1 = nullptr;
-    float last_pair_ms = 0.f, last_step_ms = 0.f;
+    float last_pair_ms = 0.f, last_step_ms = 0.f, last_tensor_ms = 0.f, last_direct_ms = 0.f;
+    std::vector<int> ev_cls;               // class of each pair launch (0 direct)
+    double tensor_flops = 0, direct_pf = 0;
     int64_t launches_per_search = 0;
     double pf_full = 0, pf_search = 0;
     bool ran = false;
@@ -445,7 +447,10 @@ TensorArgs tensor_args(const PairArgs& d, cp_plan_t p)
 cp_status enqueue_pair(cp_plan_t p, int stage, int w, float* out, cudaStream_t s, int* ev_idx)
 {
     const PairArgs a = pair_args(p, stage, w, out);
-    if (ev_idx) CP_CUDA(cudaEventRecordWithFlags(p->ev_pair[2 * (*ev_idx)], s, rec_flags(p)));
+    if (ev_idx) {
+        CP_CUDA(cudaEventRecordWithFlags(p->ev_pair[2 * (*ev_idx)], s, rec_flags(p)));
+        p->ev_cls[*ev_idx] = p->waves[w].cls;
+    }
     if (p->waves[w].cls != 0) {
         TensorArgs t = tensor_args(a, p);
         t.n_max = p->waves[w].cls;
@@ -537,14 +542,17 @@ cp_status build_graph(cp_plan_t p)
 
 cp_status read_timings(cp_plan_t p)
 {
-    float total = 0.f;
+    float total = 0.f, tens = 0.f, dir = 0.f;
     const int npl = (int)p->ev_pair.size() / 2;
     for (int i = 0; i < npl; i++) {
         float ms = 0.f;
         CP_CUDA(cudaEventElapsedTime(&ms, p->ev_pair[2 * i], p->ev_pair[2 * i + 1]));
         total += ms;
+        (p->ev_cls[i] ? tens : dir) += ms;
     }
     p->last_pair_ms = total;
+    p->last_tensor_ms = tens;
+    p->last_direct_ms = dir;
     float ms = 0.f;
     CP_CUDA(cudaEventElapsedTime(&ms, p->ev_step0, p->ev_step1));
     p->last_step_ms = ms;
@@ -758,6 +766,11 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             pf_search += pairs * (double)g.n_freq;
         }
         pf_full += pairs * (double)g.n_freq;
+        {
+            const double kk = g.hierarchical ? (double)(p->kc + (int64_t)g.top_k * (2 * p->J + 1)) : (double)g.n_freq;
+            if (p->cls[c]) p->tensor_flops += 2.0 * (double)n * (double)n * (double)p->cls[c] * kk;
+            else p->direct_pf += pairs * kk;
+        }
         // tile counts in the unit of the curve's form (a wave never mixes forms)
         p->wtile[s + 1] = p->wtile[s] + (p->cls[c] ? tensor_tiles_of(n) : tiles_of(n));
         const size_t npad = (size_t)((n + kTile - 1) / kTile * kTile);
@@ -901,6 +914,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     // events
     const int pair_launches = (int)p->waves.size() * (g.hierarchical ? 2 : 1);
     p->ev_pair.resize(2 * pair_launches);
+    p->ev_cls.assign(pair_launches, 0);
     for (auto& e : p->ev_pair) CP_CUDA(cudaEventCreate(&e));
     CP_CUDA(cudaEventCreate(&p->ev_step0));
     CP_CUDA(cudaEventCreate(&p->ev_step1));
@@ -1054,6 +1068,10 @@ cp_status cp_get_plan_info(cp_plan_t p, cp_plan_info* info)
     info->n_sm = p->n_sm;
     info->max_n = p->max_n;
     for (int k = 0; k < 5; k++) info->class_curves[k] = p->class_count[k];
+    info->last_tensor_kernel_ms = p->last_tensor_ms;
+    info->last_direct_kernel_ms = p->last_direct_ms;
+    info->tensor_flops_search = p->tensor_flops;
+    info->direct_pair_freq_search = p->direct_pf;
     return CP_OK;
 }
 
