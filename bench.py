@@ -203,6 +203,7 @@ def main():
         return
     import torch
     import paper_1412_1840_gb300 as cp
+    from paper_1412_1840_gb300.shard import max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -251,11 +252,7 @@ def main():
         barrier()
     step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
     info = plan.info()
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, device=dev)
     value = world * n * args.steps / total_s
     plan.close()
 
@@ -274,12 +271,8 @@ def main():
         for _ in range(e_steps):
             hplan.best_period_into(idx, bf, bs, per, ps)
         barrier()
-        e_s = time.perf_counter() - t0
+        e_s = max_over_ranks(time.perf_counter() - t0, device=dev)
         hplan.close()
-        if dist is not None:
-            t = torch.tensor([e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_s = float(t.item())
         h2d = b.times.nbytes + b.mags.nbytes + b.errs.nbytes
         d2h = idx.nbytes + bf.nbytes + bs.nbytes + per.nbytes + ps.nbytes + 8
         e2e = {"value": world * n * e_steps / e_s, "unit": "lightcurves/s", "h2d_bytes_per_step": int(h2d),
@@ -308,11 +301,7 @@ def main():
             ti = tplan.info()
             tk_ms.append(ti["last_tensor_kernel_ms"])
         barrier()
-        t_total = sum(te0[k].elapsed_time(te1[k]) for k in range(t_steps)) / 1e3
-        if dist is not None:
-            t = torch.tensor([t_total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_total = float(t.item())
+        t_total = max_over_ranks(sum(te0[k].elapsed_time(te1[k]) for k in range(t_steps)) / 1e3, device=dev)
         tplan.close()
         peaks = measured_peaks()
         tflops = ti["tensor_flops_search"] / (np.mean(tk_ms) / 1e3) / 1e12
