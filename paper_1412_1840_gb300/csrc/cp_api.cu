@@ -441,6 +441,7 @@ TensorArgs tensor_args(const PairArgs& d, cp_plan_t p)
     t.best_key = d.best_key;
     t.status = reinterpret_cast<int*>(status_word(p));
     t.wait_limit = p->wait_limit;
+    t.ctas_per_unit = 1;
     return t;
 }
 

@@ -187,6 +187,7 @@ struct TensorArgs {
     unsigned long long* best_key;
     int* status;
     uint32_t wait_limit;          // polls before a wait gives up (CP_ETIMEOUT)
+    int32_t ctas_per_unit;        // 1 (one CTA per unit)
 };
 
 size_t tensor_smem_bytes();

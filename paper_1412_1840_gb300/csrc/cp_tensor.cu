@@ -29,10 +29,11 @@ namespace cpk {
 
 using namespace tc;
 
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 3;
 constexpr int kTcThreads = 448;
 constexpr int kTcA = 16384;            // 128 x 64 x 2 B
 constexpr int kTcB = 32768;            // 256 x 64 x 2 B
+constexpr int kTcStageBytes = 2 * kTcA + kTcB;   // W' tiles of two M-tiles + one Z tile
 constexpr int kTcCols = 256;           // columns per unit
 constexpr int kTcProducers = 256;      // warps 6..13
 constexpr uint32_t kWaitLimit = 1u << 26;
@@ -226,17 +227,17 @@ __device__ __forceinline__ uint32_t tc_phase_u32(const TensorArgs& a, const TcUn
     return (uint32_t)(ph >> 32);
 }
 
+// Stages hold the W' tiles of two M-tiles and one Z tile: M-tiles 2P and
+// 2P+1 share every Z stage of their common K range (two TMEM accumulators).
 template <int NMAX, bool BF>
 __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* sA = smem;
-    unsigned char* sB = smem + kTcStages * kTcA;
     // producers' phase table of the current unit: (phase at the unit's first frequency, step)
-    ulonglong2* sPh = reinterpret_cast<ulonglong2*>(sB + kTcStages * kTcB);
+    ulonglong2* sPh = reinterpret_cast<ulonglong2*>(smem + kTcStages * kTcStageBytes);
     __shared__ uint64_t bar_afull[kTcStages], bar_bfull[kTcStages], bar_empty[kTcStages];
-    __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_drain;
+    __shared__ uint64_t bar_tfull, bar_tempty[2], bar_drain;
     __shared__ uint32_t s_taddr;
     __shared__ int s_abort;
     __shared__ float s_red[4][32];
@@ -248,7 +249,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
     // it never waits more than one barrier phase ahead; hence groups <= stages.
     constexpr int groups = kTcProducers / items < kTcStages ? kTcProducers / items : kTcStages;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ft = FT;
 
     if (tid == 0) {
         for (int s = 0; s < kTcStages; s++) {
@@ -256,10 +256,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
             mbar_init(&bar_bfull[s], items);
             mbar_init(&bar_empty[s], 1);
         }
-        for (int b = 0; b < 2; b++) {
-            mbar_init(&bar_tfull[b], 1);
-            mbar_init(&bar_tempty[b], 128);
-        }
+        mbar_init(&bar_tfull, 1);
+        mbar_init(&bar_tempty[0], 128);
+        mbar_init(&bar_tempty[1], 128);
         mbar_init(&bar_drain, 1);
         s_abort = 0;
         fence_mbar_init();
@@ -279,18 +278,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
         if (lane == 0) {
             uint32_t q = 0;
             bool ok = true;
-            for (int64_t u = a.unit_begin + blockIdx.x; ok && u < a.unit_end; u += gridDim.x) {
+            for (int64_t u = a.unit_begin + blockIdx.x / a.ctas_per_unit; ok && u < a.unit_end; u += gridDim.x) {
                 const TcUnit U = tc_decode(a, u);
                 if (U.empty) continue;
-                for (int I = 0; ok && I < U.nmt; I++)
-                    for (int J = 2 * I; J < U.nkc; J++, q++) {
+                for (int P = 0; ok && 2 * P < U.nmt; P++) {
+                    const int I0 = 2 * P, I1 = 2 * P + 1;
+                    for (int J = 2 * I0; J < U.nkc; J++, q++) {
+                        const bool use1 = I1 < U.nmt && J >= 2 * I1;
                         const int s = q % kTcStages;
                         if (!mbar_wait(&bar_empty[s], ((q / kTcStages) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
-                        mbar_arrive_expect_tx(&bar_afull[s], kTcA);
-                        const unsigned char* src = reinterpret_cast<const unsigned char*>(a.W16) +
-                                                   (U.wbase + tc_tile_index(I, J, U.nkc)) * (int64_t)kTcA;
-                        bulk_g2s(sA + s * kTcA, src, kTcA, &bar_afull[s]);
+                        unsigned char* st = smem + s * kTcStageBytes;
+                        const unsigned char* w16 = reinterpret_cast<const unsigned char*>(a.W16);
+                        mbar_arrive_expect_tx(&bar_afull[s], use1 ? 2 * kTcA : kTcA);
+                        bulk_g2s(st, w16 + (U.wbase + tc_tile_index(I0, J, U.nkc)) * (int64_t)kTcA, kTcA, &bar_afull[s]);
+                        if (use1)
+                            bulk_g2s(st + kTcA, w16 + (U.wbase + tc_tile_index(I1, J, U.nkc)) * (int64_t)kTcA, kTcA,
+                                     &bar_afull[s]);
                     }
+                }
             }
             if (!ok) {
                 // let copies already issued land before the CTA exits
@@ -308,28 +313,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
             constexpr uint32_t idesc = idesc_f16(128, kTcCols, BF);
             uint32_t q = 0, m = 0;
             bool ok = true;
-            for (int64_t u = a.unit_begin + blockIdx.x; ok && u < a.unit_end; u += gridDim.x) {
+            for (int64_t u = a.unit_begin + blockIdx.x / a.ctas_per_unit; ok && u < a.unit_end; u += gridDim.x) {
                 const TcUnit U = tc_decode(a, u);
                 if (U.empty) continue;
-                for (int I = 0; ok && I < U.nmt; I++, m++) {
-                    const int b = m & 1;
-                    if (!mbar_wait(&bar_tempty[b], ((m >> 1) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
+                for (int P = 0; ok && 2 * P < U.nmt; P++, m++) {
+                    const int I0 = 2 * P, I1 = 2 * P + 1;
+                    const uint32_t epar = (m & 1) ^ 1;
+                    if (!mbar_wait(&bar_tempty[0], epar, &s_abort, a.wait_limit)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t d = taddr + (uint32_t)(b * kTcCols);
-                    for (int J = 2 * I; J < U.nkc; J++, q++) {
+                    for (int J = 2 * I0; J < U.nkc; J++, q++) {
+                        const bool use1 = I1 < U.nmt && J >= 2 * I1;
                         const int s = q % kTcStages;
                         const uint32_t par = (q / kTcStages) & 1;
+                        if (J == 2 * I1 && use1) {
+                            if (!mbar_wait(&bar_tempty[1], epar, &s_abort, a.wait_limit)) { ok = false; break; }
+                        }
                         if (!mbar_wait(&bar_afull[s], par, &s_abort, a.wait_limit) ||
                             !mbar_wait(&bar_bfull[s], par, &s_abort, a.wait_limit)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t a0 = smem_u32(sA + s * kTcA), b0 = smem_u32(sB + s * kTcB);
+                        const uint32_t a0 = smem_u32(smem + s * kTcStageBytes);
+                        const uint32_t a1 = a0 + kTcA, b0 = a0 + 2 * kTcA;
 #pragma unroll
-                        for (int kk = 0; kk < 4; kk++)
-                            umma_f16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
-                                     (J > 2 * I || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < 4; kk++) {
+                            umma_f16(taddr, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                                     (J > 2 * I0 || kk > 0) ? 1u : 0u);
+                            if (use1)
+                                umma_f16(taddr + kTcCols, sw128_desc(a1 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                                         (J > 2 * I1 || kk > 0) ? 1u : 0u);
+                        }
                         umma_commit(&bar_empty[s]);
                     }
-                    if (ok) umma_commit(&bar_tfull[b]);
+                    if (ok) umma_commit(&bar_tfull);
                 }
             }
             // every MMA issued has completed before TMEM can be released
@@ -344,64 +358,76 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
         const int ew = warp - 2;                      // epilogue warp index 0..3
         uint32_t m = 0;
         bool ok = true;
-        for (int64_t u = a.unit_begin + blockIdx.x; ok && u < a.unit_end; u += gridDim.x) {
+        for (int64_t u = a.unit_begin + blockIdx.x / a.ctas_per_unit; ok && u < a.unit_end; u += gridDim.x) {
             const TcUnit U = tc_decode(a, u);
             if (U.empty) continue;
-            const CurveParams& P = a.cp[U.c];
-            const int64_t off = P.off;
+            const CurveParams& P_ = a.cp[U.c];
+            const int64_t off = P_.off;
             float an[NMAX];
 #pragma unroll
             for (int q = 0; q < NMAX; q++) an[q] = a.coef[(int64_t)U.c * a.coef_stride + q];
-            for (int I = 0; I < U.nmt; I++, m++) {
-                const int b = m & 1;
-                const int i = I * 128 + row;
-                const bool live = i < U.n;
-                // phase of this row at the unit's first frequency and its step (loaded before the wait)
-                uint64_t ph0 = 0, pstep = 0;
-                if (live) {
-                    pstep = a.ph_step[off + i];
-                    ph0 = a.ph_base[off + i] + (uint64_t)U.kfirst * pstep;
-                    if (a.stage == kStageFine) ph0 += U.peak_mult * a.ph_coarse[off + i];
+            for (int P = 0; 2 * P < U.nmt; P++, m++) {
+                // the rows' phases for both M-tiles, loaded before the wait
+                uint64_t ph0[2] = {0, 0}, pstep[2] = {0, 0};
+                bool live[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int i = (2 * P + h) * 128 + row;
+                    live[h] = i < U.n;
+                    if (live[h]) {
+                        pstep[h] = a.ph_step[off + i];
+                        ph0[h] = a.ph_base[off + i] + (uint64_t)U.kfirst * pstep[h];
+                        if (a.stage == kStageFine) ph0[h] += U.peak_mult * a.ph_coarse[off + i];
+                    }
                 }
-                mbar_wait(&bar_tfull[b], (m >> 1) & 1, &s_abort, a.wait_limit);
+                mbar_wait(&bar_tfull, m & 1, &s_abort, a.wait_limit);
                 // agree on the outcome: every epilogue thread sees the abort flag after the barrier
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (s_abort) { ok = false; break; }
                 tc_fence_after();
-                float accf[FT];
-                const uint32_t tbase = taddr + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * kTcCols);
-                // columns: f * 2 NMAX + 2 (n - 1) + {0: cos, 1: sin}
-                float v[32];
+#pragma unroll 1
+                for (int h = 0; h < 2; h++) {
+                    const bool has = 2 * P + h < U.nmt;
+                    float accf[FT];
+                    if (has) {
+                        const uint32_t tbase = taddr + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * kTcCols);
+                        float v[32];
 #pragma unroll
-                for (int f = 0; f < FT; f++) {
-                    float s1 = 0.f, c1 = 0.f;
-                    if (live) sincos2pi_turns((uint32_t)((ph0 + (uint64_t)f * pstep) >> 32), s1, c1);
-                    float cp2 = 1.f, sp2 = 0.f, cp1 = c1, sp1 = s1;
-                    float acc = 0.f;
+                        for (int f = 0; f < FT; f++) {
+                            float s1 = 0.f, c1 = 0.f;
+                            if (live[h]) sincos2pi_turns((uint32_t)((ph0[h] + (uint64_t)f * pstep[h]) >> 32), s1, c1);
+                            float cp2 = 1.f, sp2 = 0.f, cp1 = c1, sp1 = s1;
+                            float acc = 0.f;
 #pragma unroll
-                    for (int n = 1; n <= NMAX; n++) {
-                        const int col = f * 2 * NMAX + 2 * (n - 1);
-                        if ((col & 31) == 0) tmem_ld32(tbase + col, v);
-                        acc = fmaf(an[n - 1], fmaf(v[col & 31], cp1, v[(col & 31) + 1] * sp1), acc);
-                        const float cn = fmaf(2.f * c1, cp1, -cp2), sn = fmaf(2.f * c1, sp1, -sp2);
-                        cp2 = cp1; sp2 = sp1;
-                        cp1 = cn; sp1 = sn;
+                            for (int n = 1; n <= NMAX; n++) {
+                                const int col = f * 2 * NMAX + 2 * (n - 1);
+                                if ((col & 31) == 0) tmem_ld32(tbase + col, v);
+                                acc = fmaf(an[n - 1], fmaf(v[col & 31], cp1, v[(col & 31) + 1] * sp1), acc);
+                                const float cn = fmaf(2.f * c1, cp1, -cp2), sn = fmaf(2.f * c1, sp1, -sp2);
+                                cp2 = cp1; sp2 = sp1;
+                                cp1 = cn; sp1 = sn;
+                            }
+                            accf[f] = live[h] ? acc : 0.f;
+                        }
                     }
-                    accf[f] = live ? acc : 0.f;
-                }
-                tc_fence_before();
-                mbar_arrive(&bar_tempty[b]);
-                // sum over the 128 rows, fixed order
+                    // release this accumulator (always, so the phases of both buffers advance per pair)
+                    tc_fence_before();
+                    mbar_arrive(&bar_tempty[h]);
+                    if (has) {
+                        // sum over the 128 rows, fixed order
 #pragma unroll
-                for (int f = 0; f < FT; f++) {
-                    float x = accf[f];
+                        for (int f = 0; f < FT; f++) {
+                            float x = accf[f];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                    if (lane == 0) s_red[ew][f] = x;
+                            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                            if (lane == 0) s_red[ew][f] = x;
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        if (ew == 0 && lane < FT)
+                            s_acc[lane] += ((s_red[0][lane] + s_red[1][lane]) + s_red[2][lane]) + s_red[3][lane];
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                    }
                 }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                if (ew == 0 && lane < ft) s_acc[lane] += ((s_red[0][lane] + s_red[1][lane]) + s_red[2][lane]) + s_red[3][lane];
-                asm volatile("bar.sync 1, 128;" ::: "memory");
             }
             if (!ok) break;
             // unit complete: normalise and emit
@@ -409,7 +435,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                 unsigned long long key = 0ull;
                 if (lane < U.count) {
                     const float S = s_acc[lane];
-                    const float v = S * P.norm;
+                    const float v = S * P_.norm;
                     const long long kk = U.kfirst + lane;
                     if (a.stage == kStageFull) {
                         if (a.out) a.out[(int64_t)U.c * a.out_ld + kk] = v;
@@ -423,7 +449,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                             key = make_key(v, (uint32_t)(U.peak * (2 * a.fine_half + 1) + (kk + a.fine_half)));
                     }
                 }
-                if (lane < 32) s_acc[lane] = 0.f;
+                s_acc[lane] = 0.f;
                 if (a.stage != kStageCoarse) {
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -448,7 +474,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
         bool ok = true;
         // After a timeout (ok == false) a producer keeps walking the units so that
         // every producer executes the same named barriers; it skips all work.
-        for (int64_t u = a.unit_begin + blockIdx.x; u < a.unit_end; u += gridDim.x) {
+        for (int64_t u = a.unit_begin + blockIdx.x / a.ctas_per_unit; u < a.unit_end; u += gridDim.x) {
             const TcUnit U = tc_decode(a, u);
             if (U.empty) continue;
             const int64_t off = a.cp[U.c].off;
@@ -464,8 +490,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                 }
                 asm volatile("bar.sync 2, 256;" ::: "memory");
             }
-            for (int I = 0; ok && I < U.nmt; I++)
-                for (int J = 2 * I; J < U.nkc; J++, q++) {
+            for (int P = 0; ok && 2 * P < U.nmt; P++)
+                for (int J = 4 * P; J < U.nkc; J++, q++) {
                     if (!active || (int)(q % (uint32_t)groups) != grp) continue;
                     const int s = q % kTcStages;
                     const int j0 = J * 64 + g * 8;
@@ -493,7 +519,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                         cc[p] = cv; ss[p] = sv;           // n = 1
                         cm[p] = 1.f; sm[p] = 0.f;         // n = 0
                     }
-                    unsigned char* Bs = sB + s * kTcB;
+                    unsigned char* Bs = smem + s * kTcStageBytes + 2 * kTcA;
 #pragma unroll
                     for (int n = 1; n <= NMAX; n++) {
                         uint32_t pc[4], ps[4];
@@ -529,7 +555,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
 }
 
 // ---------------------------------------------------------------------------
-size_t tensor_smem_bytes() { return (size_t)kTcStages * (kTcA + kTcB) + kTcTablePoints * 16 + 1024; }
+size_t tensor_smem_bytes() { return (size_t)kTcStages * kTcStageBytes + kTcTablePoints * 16 + 1024; }
 
 int tensor_tiles_of(int n) { return tc_tiles_of(n); }
 
