@@ -171,6 +171,30 @@ __global__ void __launch_bounds__(256) k_harmonic_coef(const CurveParams* cp, in
     }
 }
 
+// Butterfly reduce-scatter over a warp: on return, lane l holds the warp-wide
+// sum of x[(l >> (5 - log2 FT)) & (FT - 1)] (every value summed over 32 lanes).
+template <int FT>
+__device__ __forceinline__ float warp_reduce_scatter(float (&x)[FT], int lane)
+{
+    constexpr int L = FT == 1 ? 0 : FT == 2 ? 1 : FT == 4 ? 2 : FT == 8 ? 3 : FT == 16 ? 4 : 5;
+#pragma unroll
+    for (int step = 0; step < L; step++) {
+        const int bit = 4 - step;
+        const int half = FT >> (step + 1);
+        const bool upper = (lane >> bit) & 1;
+#pragma unroll
+        for (int q = 0; q < half; q++) {
+            const float send = upper ? x[q] : x[q + half];
+            const float recv = __shfl_xor_sync(0xffffffffu, send, 1 << bit);
+            x[q] = (upper ? x[q + half] : x[q]) + recv;
+        }
+    }
+    float v = x[0];
+#pragma unroll
+    for (int b = 4 - L; b >= 0; b--) v += __shfl_xor_sync(0xffffffffu, v, 1 << b);
+    return v;
+}
+
 // ===========================================================================
 // k_pair_tensor
 // ===========================================================================
@@ -392,10 +416,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                     if (has) {
                         const uint32_t tbase = taddr + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * kTcCols);
                         float v[32];
+                        // the angle of odd frequencies is the even one's rotated by one frequency step
+                        float sr = 0.f, cr = 1.f, s1 = 0.f, c1 = 0.f;
+                        if (live[h]) sincos2pi_turns((uint32_t)(pstep[h] >> 32), sr, cr);
 #pragma unroll
                         for (int f = 0; f < FT; f++) {
-                            float s1 = 0.f, c1 = 0.f;
-                            if (live[h]) sincos2pi_turns((uint32_t)((ph0[h] + (uint64_t)f * pstep[h]) >> 32), s1, c1);
+                            if (live[h]) {
+                                if ((f & 1) == 0) {
+                                    sincos2pi_turns((uint32_t)((ph0[h] + (uint64_t)f * pstep[h]) >> 32), s1, c1);
+                                } else {
+                                    const float cn = fmaf(c1, cr, -s1 * sr), sn = fmaf(s1, cr, c1 * sr);
+                                    c1 = cn;
+                                    s1 = sn;
+                                }
+                            }
                             float cp2 = 1.f, sp2 = 0.f, cp1 = c1, sp1 = s1;
                             float acc = 0.f;
 #pragma unroll
@@ -415,13 +449,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                     mbar_arrive(&bar_tempty[h]);
                     if (has) {
                         // sum over the 128 rows, fixed order
-#pragma unroll
-                        for (int f = 0; f < FT; f++) {
-                            float x = accf[f];
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                            if (lane == 0) s_red[ew][f] = x;
-                        }
+                        const float x = warp_reduce_scatter<FT>(accf, lane);
+                        constexpr int SH = FT == 4 ? 3 : FT == 8 ? 2 : FT == 16 ? 1 : 0;
+                        if ((lane & ((1 << SH) - 1)) == 0) s_red[ew][lane >> SH] = x;
                         asm volatile("bar.sync 1, 128;" ::: "memory");
                         if (ew == 0 && lane < FT)
                             s_acc[lane] += ((s_red[0][lane] + s_red[1][lane]) + s_red[2][lane]) + s_red[3][lane];
