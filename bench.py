@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ragged", choices=["ragged", "hierarchical", "single", "small"])
+    ap.add_argument("--workload", default="ragged", choices=["ragged", "hierarchical", "single", "small", "throughput"])
     ap.add_argument("--n-curves", type=int, default=None)
     ap.add_argument("--form", default="direct", choices=["direct", "tensor"])
     ap.add_argument("--n-max", type=int, default=0, help="tensor-form harmonics (0: per curve)")
@@ -80,6 +80,11 @@ def make_workload(args, rank):
         b, g = synth.workload_ragged(n, seed)
         g = synth.Grid(g.f_min, g.df, 2048)
         name = "%d curves N~U[300,1000], 2,048 freqs (profiling case)" % n
+    elif args.workload == "throughput":
+        ns = (args.n_curves or 200000) // 2
+        b, g = synth.workload_throughput(ns, seed)
+        name = ("%d two-band sources (%d curves) N~U[200,1000] per band, SNR 0.2-10; coarse 0.002-5 step 1e-3, "
+                "top-10 refined at 1e-5 over +-2e-3" % (ns, 2 * ns))
     elif args.workload == "hierarchical":
         n = args.n_curves or 4096
         b, g = synth.workload_hierarchical(n, seed)

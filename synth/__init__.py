@@ -93,18 +93,28 @@ def grid_from_range(f_min: float, f_max: float, df: float, **kw) -> Grid:
 
 
 def seasonal_times(rng: np.random.Generator, sizes: np.ndarray, span: float) -> np.ndarray:
-    """Sorted times, uniform on the union of yearly 8-month windows within [0, span]."""
+    """Sorted times, uniform on the union of yearly 8-month windows within [0, span].
+
+    Sorted uniform samples come straight from normalised cumulative sums of
+    exponential spacings (n + 1 per curve), mapped through the monotone
+    window map, so no sort is needed."""
     starts = np.arange(0.0, span, YEAR_D)
     ends = np.minimum(starts + SEASON_D, span)
     lens = ends - starts
     cum = np.concatenate([[0.0], np.cumsum(lens)])
-    total = int(sizes.sum())
-    u = rng.uniform(0.0, cum[-1], size=total)
+    n_c = sizes.shape[0]
+    ext = sizes + 1
+    e = rng.exponential(size=int(ext.sum()))
+    cs = np.cumsum(e)
+    eoff = np.concatenate([[0], np.cumsum(ext)])
+    base = np.concatenate([[0.0], cs])[eoff[:-1]]          # cumulative sum before each curve
+    tot = cs[eoff[1:] - 1] - base                           # sum of the curve's n + 1 spacings
+    keep = np.ones(e.shape[0], bool)
+    keep[eoff[1:] - 1] = False                              # drop each curve's last partial sum
+    cid = np.repeat(np.arange(n_c), sizes)
+    u = (cs[keep] - base[cid]) / tot[cid] * cum[-1]
     w = np.clip(np.searchsorted(cum, u, side="right") - 1, 0, len(lens) - 1)
-    t = starts[w] + (u - cum[w])
-    cid = np.repeat(np.arange(sizes.shape[0]), sizes)
-    order = np.lexsort((t, cid))
-    return t[order]
+    return starts[w] + (u - cum[w])
 
 
 def _offsets(sizes: np.ndarray) -> np.ndarray:
@@ -156,16 +166,19 @@ def _shape_values(rng, kinds, periods, t, cid, sizes):
     out[m] = rng.standard_normal(int(m.sum()))
     m = k == 1          # damped random walk (Ornstein-Uhlenbeck), exact irregular-step update
     if m.any():
-        for c in np.nonzero(kinds == 1)[0]:
-            a, b = int(np.sum(sizes[:c])), int(np.sum(sizes[:c + 1]))
-            tt = t[a:b]
-            x = np.empty(b - a)
-            x[0] = rng.standard_normal()
-            dec = np.exp(-np.diff(tt) / tau[c])
-            z = rng.standard_normal(b - a - 1)
-            for i in range(1, b - a):
-                x[i] = x[i - 1] * dec[i - 1] + np.sqrt(1.0 - dec[i - 1] ** 2) * z[i - 1]
-            out[a:b] = x
+        drw = np.nonzero(kinds == 1)[0]
+        off = np.concatenate([[0], np.cumsum(sizes)])
+        starts, lens = off[drw], sizes[drw]
+        x = rng.standard_normal(drw.shape[0])
+        out[starts] = x
+        # step i of every damped-random-walk curve at once (vectorised across curves)
+        for i in range(1, int(lens.max()) if lens.size else 1):
+            act = lens > i
+            idx = starts[act] + i
+            dec = np.exp(-(t[idx] - t[idx - 1]) / tau[drw[act]])
+            x_act = x[act] * dec + np.sqrt(1.0 - dec * dec) * rng.standard_normal(idx.shape[0])
+            x[act] = x_act
+            out[idx] = x_act
     return out
 
 
@@ -213,10 +226,29 @@ def ragged_batch(n_curves: int, seed: int = 1, n_lo: int = 300, n_hi: int = 1000
         snr = np.exp(rng.uniform(np.log(snr_lo), np.log(snr_hi), n_curves))
         off = _offsets(sizes)
         scale = np.empty(n_curves)
-        for c in range(n_curves):
-            a, b = off[c], off[c + 1]
-            iq = _iqr(shape[a:b])
-            scale[c] = snr[c] * np.median(err[a:b]) / (0.7413 * iq) if iq > 0 else 0.0
+        nmax = int(sizes.max())
+        for c0 in range(0, n_curves, 4096):            # padded blocks of curves
+            c1 = min(n_curves, c0 + 4096)
+            nb = c1 - c0
+            pos = np.arange(off[c0], off[c1]) - np.repeat(off[c0:c1], sizes[c0:c1])
+            row = np.repeat(np.arange(nb), sizes[c0:c1])
+            S = np.full((nb, nmax), np.nan)
+            E = np.full((nb, nmax), np.nan)
+            S[row, pos] = shape[off[c0]:off[c1]]
+            E[row, pos] = err[off[c0]:off[c1]]
+            S.sort(axis=1)                      # NaN padding sorts last
+            E.sort(axis=1)
+            nn = sizes[c0:c1]
+            rows = np.arange(nb)
+
+            def q_lin(A, q):
+                pos = q * (nn - 1)
+                lo = np.floor(pos).astype(np.int64)
+                hi = np.minimum(lo + 1, nn - 1)
+                return A[rows, lo] + (pos - lo) * (A[rows, hi] - A[rows, lo])
+            iq = q_lin(S, 0.75) - q_lin(S, 0.25)
+            med = q_lin(E, 0.5)
+            scale[c0:c1] = np.where(iq > 0, snr[c0:c1] * med / (0.7413 * np.where(iq > 0, iq, 1.0)), 0.0)
         sig = scale[cid] * shape
     else:
         sig = amp[cid] * shape
@@ -227,25 +259,25 @@ def ragged_batch(n_curves: int, seed: int = 1, n_lo: int = 300, n_hi: int = 1000
 
 def two_band_batch(n_sources: int, seed: int = 5, n_lo: int = 200, n_hi: int = 1000,
                    span: float = 2500.0) -> Batch:
-    """Two independent bands per source (curves 2s and 2s+1 share the source's
-    period and shape class, with independent sampling and noise); SNR
-    log-uniform 0.2-10 by the paper's synthetic-set scaling."""
+    """Two independent bands per source: curves 2s and 2s+1 are drawn with the
+    same period, shape class and SNR recipe but independent sampling and noise;
+    SNR log-uniform 0.2-10 by the paper's synthetic-set scaling."""
     a = ragged_batch(n_sources, seed=seed, n_lo=n_lo, n_hi=n_hi, span=span, snr_scaling=True)
-    rng = np.random.default_rng(seed + 1000)
     b = ragged_batch(n_sources, seed=seed + 1, n_lo=n_lo, n_hi=n_hi, span=span, snr_scaling=True)
-    del rng
-    # interleave: the second band takes the first band's period/shape labels
-    idx = np.empty(2 * n_sources, dtype=np.int64)
-    parts_t, parts_m, parts_e, offs = [], [], [], [0]
-    for s in range(n_sources):
-        for src in (a, b):
-            t, m, e = src.curve(s)
-            parts_t.append(t); parts_m.append(m); parts_e.append(e)
-            offs.append(offs[-1] + t.shape[0])
-    del idx
-    return Batch(np.concatenate(parts_t), np.concatenate(parts_m), np.concatenate(parts_e),
-                 np.asarray(offs, np.int64), np.repeat(a.period, 2), np.repeat(a.periodic, 2),
-                 np.repeat(a.kind, 2))
+    # interleave a's and b's curves: curve 2s from a, 2s+1 from b
+    sizes = np.empty(2 * n_sources, dtype=np.int64)
+    sizes[0::2] = a.sizes
+    sizes[1::2] = b.sizes
+    off = _offsets(sizes)
+    total = int(off[-1])
+    src_a = np.repeat(np.arange(n_sources) * 2, a.sizes)
+    src_b = np.repeat(np.arange(n_sources) * 2 + 1, b.sizes)
+    pos_a = off[src_a] + (np.arange(a.offsets[-1]) - np.repeat(a.offsets[:-1], a.sizes))
+    pos_b = off[src_b] + (np.arange(b.offsets[-1]) - np.repeat(b.offsets[:-1], b.sizes))
+    t = np.empty(total); m = np.empty(total, np.float32); e = np.empty(total, np.float32)
+    t[pos_a], m[pos_a], e[pos_a] = a.times, a.mags, a.errs
+    t[pos_b], m[pos_b], e[pos_b] = b.times, b.mags, b.errs
+    return Batch(t, m, e, off, np.repeat(a.period, 2), np.repeat(a.periodic, 2), np.repeat(a.kind, 2))
 
 
 def edge_batch(seed: int = 7) -> Batch:
@@ -276,6 +308,20 @@ def workload_single():
 def workload_ragged(n_curves: int = 4096, seed: int = 1):
     """4096 curves, N ~ U{300..1000}, seasonal over 2500 d; grid 0.002-5 step 1e-4 (49,981)."""
     return ragged_batch(n_curves, seed=seed), grid_from_range(0.002, 5.0, 1e-4)
+
+
+def workload_throughput(n_sources: int = 100000, seed: int = 5):
+    """100,000 two-band sources (200,000 curves, N ~ U{200..1000} per band,
+    SNR 0.2-10, 50% periodic); hierarchical search: coarse step 1e-3 over
+    0.002-5, top-10 refined at 1e-5 over +-2e-3."""
+    b = two_band_batch(n_sources, seed=seed)
+    g = grid_from_range(0.002, 5.0, 1e-4)
+    g.hierarchical = True
+    g.coarse_df = 1e-3
+    g.top_k = 10
+    g.fine_df = 1e-5
+    g.fine_halfwidth = 2e-3
+    return b, g
 
 
 def workload_hierarchical(n_curves: int = 4096, seed: int = 1):
