@@ -28,11 +28,13 @@ I64 = ctypes.c_int64
 PD = ctypes.POINTER(ctypes.c_double)
 PF = ctypes.POINTER(ctypes.c_float)
 PI64 = ctypes.POINTER(ctypes.c_int64)
+PI32 = ctypes.POINTER(ctypes.c_int32)
 
 
 class OrcGrid(ctypes.Structure):
     _fields_ = [("f_min", D), ("df", D), ("n_freq", I64), ("hierarchical", ctypes.c_int),
-                ("coarse_df", D), ("top_k", I64), ("fine_df", D), ("fine_halfwidth", D)]
+                ("coarse_df", D), ("top_k", I64), ("fine_df", D), ("fine_halfwidth", D),
+                ("n_bands", I64), ("trials_per_band", I64)]
 
 
 class OrcOptions(ctypes.Structure):
@@ -83,6 +85,18 @@ def lib():
                                      ctypes.POINTER(OrcOptions), ctypes.POINTER(OrcResult)]
         L.orc_batch_nckp.restype = None
         L.orc_batch_nckp.argtypes = [PD, PF, PF, PI64, I64, PD, PD, I64, PD]
+        L.orc_bands_of.restype = None; L.orc_bands_of.argtypes = [PD, I64, PI32]
+        L.orc_band_derivative_sums.restype = None
+        L.orc_band_derivative_sums.argtypes = [PD, PD, I64, PI32, PD]
+        L.orc_band_order.restype = None; L.orc_band_order.argtypes = [PD, PI32]
+        L.orc_spectral_window.restype = None
+        L.orc_spectral_window.argtypes = [PD, I64, PI32, ctypes.c_int32, D, D, I64, PD]
+        L.orc_is_one_day.restype = ctypes.c_int; L.orc_is_one_day.argtypes = [D]
+        L.orc_window_trials.restype = I64; L.orc_window_trials.argtypes = [PD, I64, D, D, I64, PI64]
+        L.orc_bands_trials.restype = None
+        L.orc_bands_trials.argtypes = [PD, PD, I64, D, D, I64, I64, I64, PI64]
+        L.orc_batch_bands_trials.restype = None
+        L.orc_batch_bands_trials.argtypes = [PD, PF, PI64, I64, D, D, I64, I64, I64, PI64]
         _lib = L
     return _lib
 
@@ -155,9 +169,72 @@ def top_local_maxima(v, top_k) -> np.ndarray:
     return out[:n]
 
 
+# ---- bands method, Section 3.1 ---------------------------------------------
+
+
+def bands_of(y) -> np.ndarray:
+    """Band 0..9 of every sample (ten equal-count magnitude bands)."""
+    y, py = _d(y); out = np.empty(y.shape[0], np.int32)
+    lib().orc_bands_of(py, y.shape[0], out.ctypes.data_as(PI32))
+    return out
+
+
+def band_derivative_sums(t, y, band) -> np.ndarray:
+    t, pt = _d(t); y, py = _d(y); b = np.ascontiguousarray(band, np.int32); out = np.empty(10)
+    lib().orc_band_derivative_sums(pt, py, t.shape[0], b.ctypes.data_as(PI32), out.ctypes.data_as(PD))
+    return out
+
+
+def band_order(D) -> np.ndarray:
+    D, pD = _d(D); out = np.empty(10, np.int32)
+    lib().orc_band_order(pD, out.ctypes.data_as(PI32))
+    return out
+
+
+def spectral_window(t, band, j, f_min, df, nk) -> np.ndarray:
+    t, pt = _d(t); b = np.ascontiguousarray(band, np.int32); out = np.empty(int(nk))
+    lib().orc_spectral_window(pt, t.shape[0], b.ctypes.data_as(PI32), int(j), float(f_min), float(df), int(nk),
+                              out.ctypes.data_as(PD))
+    return out
+
+
+def is_one_day(f) -> bool:
+    return bool(lib().orc_is_one_day(float(f)))
+
+
+def window_trials(S, f_min, df, n_t) -> np.ndarray:
+    S, pS = _d(S); out = np.empty(max(int(n_t), 1), np.int64)
+    lib().orc_window_trials(pS, S.shape[0], float(f_min), float(df), int(n_t), out.ctypes.data_as(PI64))
+    return out[:int(n_t)]
+
+
+def bands_trials(t, y, f_min, df, nk, n_bands, n_t) -> np.ndarray:
+    """[n_bands, n_t] trial grid indices of one curve (-1 = none)."""
+    t, pt = _d(t); y, py = _d(y); out = np.empty((int(n_bands), int(n_t)), np.int64)
+    lib().orc_bands_trials(pt, py, t.shape[0], float(f_min), float(df), int(nk), int(n_bands), int(n_t),
+                           out.ctypes.data_as(PI64))
+    return out
+
+
+def batch_bands_trials(batch, grid) -> np.ndarray:
+    """[n_curves, n_bands * trials_per_band] trial grid indices of a CSR batch."""
+    t = np.ascontiguousarray(batch.times, np.float64)
+    m = np.ascontiguousarray(batch.mags, np.float32)
+    off = np.ascontiguousarray(batch.offsets, np.int64)
+    nc = off.shape[0] - 1
+    L = int(grid.n_bands) * int(grid.trials_per_band)
+    out = np.empty((nc, L), np.int64)
+    lib().orc_batch_bands_trials(t.ctypes.data_as(PD), m.ctypes.data_as(PF), off.ctypes.data_as(PI64), nc,
+                                 float(grid.f_min), float(grid.df), int(grid.n_freq), int(grid.n_bands),
+                                 int(grid.trials_per_band), out.ctypes.data_as(PI64))
+    return out
+
+
 def _grid(g) -> OrcGrid:
-    return OrcGrid(g.f_min, g.df, g.n_freq, int(bool(g.hierarchical)), g.coarse_df or 0.0,
-                   int(g.top_k or 0), g.fine_df or 0.0, g.fine_halfwidth or 0.0)
+    mode = 2 if getattr(g, "bands", False) else int(bool(g.hierarchical))
+    return OrcGrid(g.f_min, g.df, g.n_freq, mode, g.coarse_df or 0.0,
+                   int(g.top_k or 0), g.fine_df or 0.0, g.fine_halfwidth or 0.0,
+                   int(getattr(g, "n_bands", 0) or 0), int(getattr(g, "trials_per_band", 0) or 0))
 
 
 def _opts(sigma_t_mode, sigma_t, per_curve, alpha):

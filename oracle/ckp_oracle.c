@@ -32,7 +32,14 @@
  *     sorted magnitudes (the rule's own footnote), the middle value excluded
  *     for odd N; S = 0 when Q3 == Q1;
  *   argmax ties go to the lowest frequency index;
- *   SNR bins are left-closed, pSNR >= 20 falls in the last bin.
+ *   SNR bins are left-closed, pSNR >= 20 falls in the last bin;
+ *   bands method: derivatives between consecutive samples as given (time
+ *     order), d_i = 0 when t_{i+1} == t_i; d_i belongs to the band of its left
+ *     sample; band k holds the samples of magnitude rank [floor(kN/10),
+ *     floor((k+1)N/10)) (ties by sample index); bands ordered by D_j
+ *     descending, ties to the lower band; one-day frequencies keep their
+ *     values in the local-maximum test and are only skipped as candidates;
+ *     a one-sample band's window is exactly 1; missing entries are -1.
  */
 #include <math.h>
 #include <stdint.h>
@@ -234,6 +241,7 @@ typedef struct {
     double coarse_df;
     int64_t top_k;
     double fine_df, fine_halfwidth;
+    int64_t n_bands, trials_per_band;   /* bands method (hierarchical == 2) */
 } orc_grid;
 
 typedef struct {
@@ -250,6 +258,9 @@ typedef struct {
     int is_periodic;
     double psnr, sigma_y, sigma_t, ip;
 } orc_result;
+
+void orc_bands_trials(const double *t, const double *y, int64_t n, double f_min, double df, int64_t nk,
+                      int64_t n_bands, int64_t n_t, int64_t *out_k);
 
 static double curve_sigma_t(const orc_options *o, const double *y, int64_t n, int64_t c)
 {
@@ -272,7 +283,10 @@ static int64_t n_coarse(const orc_grid *g)
  * top_k local maxima, each refined over f_peak + j fine_df, |j| <= J with
  * J = round(fine_halfwidth / fine_df), points outside [f_min, f_max]
  * skipped; best over (rank, j) by value, ties to the lower candidate
- * index rank*(2J+1) + (j+J), which is reported as best_idx. */
+ * index rank*(2J+1) + (j+J), which is reported as best_idx.
+ * Bands method (hierarchical == 2): the n_bands * trials_per_band trial grid
+ * indices of Section 3.1; best over the trial list by value, ties to the
+ * lower list position; best_idx is the winning grid index k. */
 void orc_curve_best(const double *t, const double *y, const double *e, int64_t n, int64_t c,
                     const orc_grid *g, const orc_options *o, orc_result *r)
 {
@@ -283,7 +297,33 @@ void orc_curve_best(const double *t, const double *y, const double *e, int64_t n
     r->ip = orc_information_potential(y, n, sy);
     r->psnr = orc_psnr(y, e, n, o->alpha);
     double f_max = g->f_min + (double)(g->n_freq - 1) * g->df;
-    if (!g->hierarchical) {
+    if (g->hierarchical == 2) {
+        int64_t L = g->n_bands * g->trials_per_band, m = 0;
+        int64_t *ks = (int64_t *)malloc((size_t)(L > 0 ? L : 1) * sizeof(int64_t));
+        double *fr = (double *)malloc((size_t)(L > 0 ? L : 1) * sizeof(double));
+        double *v = (double *)malloc((size_t)(L > 0 ? L : 1) * sizeof(double));
+        int64_t *kk = (int64_t *)malloc((size_t)(L > 0 ? L : 1) * sizeof(int64_t));
+        orc_bands_trials(t, y, n, g->f_min, g->df, g->n_freq, g->n_bands, g->trials_per_band, ks);
+        for (int64_t q = 0; q < L; q++)
+            if (ks[q] >= 0) {
+                kk[m] = ks[q];
+                fr[m++] = g->f_min + (double)ks[q] * g->df;
+            }
+        orc_nckp(t, y, n, sy, st, fr, m, v);
+        r->best_idx = -1;
+        r->best_freq = NAN;
+        r->best_stat = NAN;
+        if (m > 0) {
+            int64_t b = orc_argmax(v, m);
+            r->best_idx = kk[b];
+            r->best_freq = fr[b];
+            r->best_stat = v[b];
+        }
+        free(kk);
+        free(v);
+        free(fr);
+        free(ks);
+    } else if (!g->hierarchical) {
         double *fr = (double *)malloc((size_t)g->n_freq * sizeof(double));
         double *v = (double *)malloc((size_t)g->n_freq * sizeof(double));
         for (int64_t k = 0; k < g->n_freq; k++)
@@ -405,4 +445,168 @@ void orc_batch_nckp(const double *times, const float *mags, const float *errs,
     }
     free(ips);
     free(sys);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Bands method, Section 3.1                                               */
+/* ---------------------------------------------------------------------- */
+
+typedef struct { double y; int64_t i; } orc_rank_item;
+
+static int cmp_rank_item(const void *a, const void *b)
+{
+    const orc_rank_item *x = (const orc_rank_item *)a, *z = (const orc_rank_item *)b;
+    if (x->y < z->y) return -1;
+    if (x->y > z->y) return 1;
+    return (x->i > z->i) - (x->i < z->i);
+}
+
+/* Step 2: ten bands of equal sample count on the magnitude axis.  Band k
+ * holds the samples of magnitude rank r with floor(kN/10) <= r < floor((k+1)N/10)
+ * (rank 0 = faintest value, i.e. smallest magnitude number; equal magnitudes
+ * ranked by sample index). */
+void orc_bands_of(const double *y, int64_t n, int32_t *band)
+{
+    orc_rank_item *r = (orc_rank_item *)malloc((size_t)(n > 0 ? n : 1) * sizeof(orc_rank_item));
+    for (int64_t i = 0; i < n; i++) {
+        r[i].y = y[i];
+        r[i].i = i;
+    }
+    qsort(r, (size_t)n, sizeof(orc_rank_item), cmp_rank_item);
+    for (int64_t rank = 0; rank < n; rank++) {
+        int k = 0;
+        while (k < 9 && rank >= ((int64_t)(k + 1) * n) / 10)
+            k++;
+        band[r[rank].i] = k;
+    }
+    free(r);
+}
+
+/* Steps 1 and 3: d_i = (x_{i+1} - x_i) / (t_{i+1} - t_i) for consecutive
+ * samples (0 where the two times are equal); D_k = sum of |d_i| over the d_i
+ * whose sample i lies in band k. */
+void orc_band_derivative_sums(const double *t, const double *y, int64_t n, const int32_t *band, double *D)
+{
+    for (int k = 0; k < 10; k++)
+        D[k] = 0.0;
+    for (int64_t i = 0; i + 1 < n; i++) {
+        double dt = t[i + 1] - t[i];
+        double d = dt != 0.0 ? (y[i + 1] - y[i]) / dt : 0.0;
+        D[band[i]] += fabs(d);
+    }
+}
+
+/* Step 4: the ten bands in descending order of D (equal D: lower band first). */
+void orc_band_order(const double *D, int32_t *order)
+{
+    for (int k = 0; k < 10; k++)
+        order[k] = k;
+    for (int a = 1; a < 10; a++) {
+        int32_t v = order[a];
+        int b = a;
+        while (b > 0 && D[order[b - 1]] < D[v]) {
+            order[b] = order[b - 1];
+            b--;
+        }
+        order[b] = v;
+    }
+}
+
+/* Step 5, Eq. (bands): S_j(f) = |sum_{i in B_j} exp(i 2 pi f t_i)|^2 on the
+ * linear grid f_k = f_min + k df, k < nk.  A band of one sample has the
+ * exact value |exp(i x)|^2 = 1 at every f (cos^2 + sin^2 would add rounding
+ * noise that alone would decide its local maxima). */
+void orc_spectral_window(const double *t, int64_t n, const int32_t *band, int32_t j, double f_min, double df,
+                         int64_t nk, double *S)
+{
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; i++)
+        m += band[i] == j;
+    for (int64_t k = 0; k < nk; k++) {
+        if (m <= 1) {
+            S[k] = (double)m;
+            continue;
+        }
+        double f = f_min + (double)k * df, re = 0.0, im = 0.0;
+        for (int64_t i = 0; i < n; i++)
+            if (band[i] == j) {
+                re += cos(2.0 * ORC_PI * f * t[i]);
+                im += sin(2.0 * ORC_PI * f * t[i]);
+            }
+        S[k] = re * re + im * im;
+    }
+}
+
+/* The one-day pseudo-sampling period: periods with |P - 1| < 1e-4 day. */
+int orc_is_one_day(double f)
+{
+    return f > 0.0 && fabs(1.0 / f - 1.0) < 1e-4;
+}
+
+/* Step 6 for one band: grid indices of the n_t highest local maxima of S
+ * (local maximum as in orc_top_local_maxima; value descending, ties to the
+ * lower index), the one-day frequencies left out before the choice.
+ * Writes n_t entries, -1 after the last one found; returns the count. */
+int64_t orc_window_trials(const double *S, int64_t nk, double f_min, double df, int64_t n_t, int64_t *out_k)
+{
+    int64_t *pk = (int64_t *)malloc((size_t)(n_t > 0 ? n_t : 1) * sizeof(int64_t));
+    /* a one-day point keeps its value in its neighbours' comparisons; it is
+     * only skipped as a candidate */
+    int64_t cnt = 0;
+    for (int64_t k = 0; k < nk; k++) {
+        int left_ok = (k == 0) || (S[k] > S[k - 1]);
+        int right_ok = (k == nk - 1) || (S[k] >= S[k + 1]);
+        if (!(left_ok && right_ok) || orc_is_one_day(f_min + (double)k * df))
+            continue;
+        int64_t pos = cnt < n_t ? cnt : n_t;
+        while (pos > 0 && S[k] > S[pk[pos - 1]])
+            pos--;
+        if (pos >= n_t)
+            continue;
+        int64_t last = cnt < n_t ? cnt : n_t - 1;
+        for (int64_t m = last; m > pos; m--)
+            pk[m] = pk[m - 1];
+        pk[pos] = k;
+        if (cnt < n_t)
+            cnt++;
+    }
+    for (int64_t r = 0; r < n_t; r++)
+        out_k[r] = r < cnt ? pk[r] : -1;
+    free(pk);
+    return cnt;
+}
+
+/* All six steps: n_bands * n_t trial grid indices, band-rank major
+ * (out_k[b * n_t + r] = r-th trial of the b-th band in D order). */
+void orc_bands_trials(const double *t, const double *y, int64_t n, double f_min, double df, int64_t nk,
+                      int64_t n_bands, int64_t n_t, int64_t *out_k)
+{
+    int32_t *band = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    double D[10];
+    int32_t order[10];
+    orc_bands_of(y, n, band);
+    orc_band_derivative_sums(t, y, n, band, D);
+    orc_band_order(D, order);
+    double *S = (double *)malloc((size_t)(nk > 0 ? nk : 1) * sizeof(double));
+    for (int64_t b = 0; b < n_bands; b++) {
+        orc_spectral_window(t, n, band, order[b], f_min, df, nk, S);
+        orc_window_trials(S, nk, f_min, df, n_t, out_k + b * n_t);
+    }
+    free(S);
+    free(band);
+}
+
+/* Trial lists of a CSR batch, parallel over curves: out_k[c * n_bands * n_t + ...]. */
+void orc_batch_bands_trials(const double *times, const float *mags, const int64_t *offsets, int64_t n_curves,
+                            double f_min, double df, int64_t nk, int64_t n_bands, int64_t n_t, int64_t *out_k)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < n_curves; c++) {
+        int64_t a = offsets[c], n = offsets[c + 1] - offsets[c];
+        double *y = (double *)malloc((size_t)n * sizeof(double));
+        for (int64_t i = 0; i < n; i++)
+            y[i] = (double)mags[a + i];
+        orc_bands_trials(times + a, y, n, f_min, df, nk, n_bands, n_t, out_k + c * n_bands * n_t);
+        free(y);
+    }
 }

@@ -68,7 +68,9 @@ SHAPES = {0: "white noise", 1: "damped random walk", 2: "sinusoid (1-3 harmonics
 @dataclasses.dataclass
 class Grid:
     """Uniform trial-frequency grid f_k = f_min + k*df, k = 0..n_freq-1 (1/day),
-    plus the coarse/fine parameters of the hierarchical search."""
+    plus the coarse/fine parameters of the hierarchical search, or (bands=True)
+    the band and trial counts of the bands method of Section 3.1, whose
+    spectral windows run on this grid."""
     f_min: float
     df: float
     n_freq: int
@@ -77,6 +79,9 @@ class Grid:
     top_k: int = 0
     fine_df: float = 0.0
     fine_halfwidth: float = 0.0
+    bands: bool = False
+    n_bands: int = 0
+    trials_per_band: int = 0
 
     @property
     def f_max(self) -> float:
@@ -308,6 +313,15 @@ def workload_single():
 def workload_ragged(n_curves: int = 4096, seed: int = 1):
     """4096 curves, N ~ U{300..1000}, seasonal over 2500 d; grid 0.002-5 step 1e-4 (49,981)."""
     return ragged_batch(n_curves, seed=seed), grid_from_range(0.002, 5.0, 1e-4)
+
+
+def workload_bands(n_curves: int = 4096, seed: int = 1):
+    """Same batch; the bands method of Section 3.1 at the paper's operating
+    point N_b = 3, N_t = 150, spectral windows on 0.00125-3 1/d (periods
+    0.33-800 d) at step 1e-4 (29,988 frequencies; the paper gives no step)."""
+    b = ragged_batch(n_curves, seed=seed)
+    g = grid_from_range(0.00125, 3.0, 1e-4, bands=True, n_bands=3, trials_per_band=150)
+    return b, g
 
 
 def workload_throughput(n_sources: int = 100000, seed: int = 5):
