@@ -245,7 +245,9 @@ def test_hierarchical_reduces_to_full_grid():
     gh = synth.Grid(g.f_min, g.df, g.n_freq, True, g.df, 200, g.df, 2 * g.df)
     hier = oracle.batch_best(b, gh, sigma_t=0.3)
     np.testing.assert_allclose(hier["best_freq"], full["best_freq"], rtol=0, atol=1e-12)
-    np.testing.assert_allclose(hier["best_stat"], full["best_stat"], rtol=1e-14)
+    # the two routes reach the same grid frequency up to one FP64 ulp (f_min + k df versus
+    # f_peak + j fine_df); over a 300-day span that ulp moves nCKP by ~1e-13 relative
+    np.testing.assert_allclose(hier["best_stat"], full["best_stat"], rtol=1e-12)
 
 
 def test_noiseless_sinusoid_recovered_within_one_step():
