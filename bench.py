@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ragged", choices=["ragged", "hierarchical", "single", "small", "throughput"])
+    ap.add_argument("--workload", default="ragged", choices=["ragged", "hierarchical", "bands", "single", "small", "throughput"])
     ap.add_argument("--n-curves", type=int, default=None)
     ap.add_argument("--form", default="direct", choices=["direct", "tensor"])
     ap.add_argument("--n-max", type=int, default=0, help="tensor-form harmonics (0: per curve)")
@@ -85,6 +85,11 @@ def make_workload(args, rank):
         b, g = synth.workload_throughput(ns, seed)
         name = ("%d two-band sources (%d curves) N~U[200,1000] per band, SNR 0.2-10; coarse 0.002-5 step 1e-3, "
                 "top-10 refined at 1e-5 over +-2e-3" % (ns, 2 * ns))
+    elif args.workload == "bands":
+        n = args.n_curves or 4096
+        b, g = synth.workload_bands(n, seed)
+        name = ("%d curves N~U[300,1000] seasonal 2500 d; bands method N_b=3, N_t=150 on 0.00125-3 step 1e-4 "
+                "(29,988 window freqs, 450 trial freqs per curve)" % n)
     elif args.workload == "hierarchical":
         n = args.n_curves or 4096
         b, g = synth.workload_hierarchical(n, seed)
@@ -166,6 +171,14 @@ def cpu_baseline(b, g, target_s=15.0, max_curves=8):
     oracle.batch_nckp(sub, st, fs)
     dt = time.perf_counter() - t0
     n2k_sample = float(np.sum(sub.sizes.astype(np.float64) ** 2)) * k_sample
+    if getattr(g, "bands", False):
+        # the whole bands search (windows + nCKP at the trials) on the sampled curves, per curve
+        t0 = time.perf_counter()
+        oracle.batch_best(sub, g, sigma_t_mode=2)
+        dt = time.perf_counter() - t0
+        return {"value": nc / dt, "unit": "lightcurves/s", "cores": min(cores, nc), "kind": "oracle",
+                "sample": "%d curves, whole bands search (FP64 spectral windows and N^2 double loop at the "
+                          "trials, OpenMP over curves), %.1f s" % (nc, dt), "seconds": dt}
     if g.hierarchical:
         kc = int(np.floor((g.f_max - g.f_min) / g.coarse_df + 0.5)) + 1
         k_full = kc + g.top_k * (2 * int(round(g.fine_halfwidth / g.fine_df)) + 1)
@@ -364,6 +377,10 @@ def main():
                             "avg_launch_ms": float(info["last_tensor_kernel_ms"])}
     if tensor is not None:
         line["tensor"] = tensor
+    if getattr(g, "bands", False):
+        line["bands"] = {"kernels": "k_bands + k_window", "ms_per_step": float(info["last_bands_kernel_ms"]),
+                         "window_terms_per_s": info["window_terms_search"] / (info["last_bands_kernel_ms"] / 1e3),
+                         "trials_per_curve": int(g.n_bands * g.trials_per_band)}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(b, g)
         line["cpu_baseline"].pop("seconds", None)

@@ -69,16 +69,41 @@ enum { CP_MEM_HOST = 0, CP_MEM_DEVICE = 1 };
  * skipped; the best over all refined candidates by value, ties to the lower
  * candidate index rank*(2J+1) + (j+J).  cp_periodogram always evaluates the
  * uniform grid.
+ *
+ * hierarchical == CP_SEARCH_BANDS runs the trial-period extraction of
+ * Section 3.1 (the bands method) on the device before the pair sums:
+ *   1. d_i = (y_{i+1} - y_i) / (t_{i+1} - t_i) over consecutive samples in
+ *      the order given (0 where the two times are equal);
+ *   2. ten bands of equal count on the magnitude axis: band b holds the
+ *      samples of magnitude rank r (ascending, equal values by sample index)
+ *      with floor(bN/10) <= r < floor((b+1)N/10);
+ *   3. D_b = sum of |d_i| over the d_i whose sample i is in band b (FP64);
+ *   4. the n_bands bands of largest D (equal D: lower band first);
+ *   5. for each, the spectral window S_b(f) = |sum_{i in b} exp(i 2 pi f t_i)|^2
+ *      of Eq. (bands) on the uniform grid above (n_freq <= CP_BANDS_MAX_FREQ);
+ *   6. the trials_per_band highest local maxima of S_b (local maximum and
+ *      tie rule as above), leaving out the one-day frequencies
+ *      |1/f - 1| < 1e-4 (FP64).
+ * nCKP is then evaluated at the n_bands * trials_per_band trial grid
+ * frequencies only, and the best is the largest, ties to the lower
+ * position in the band-major trial list.  best_idx is the winning grid
+ * index k.  cp_trial_frequencies returns the list and its nCKP values.
  */
+enum { CP_SEARCH_FULL = 0, CP_SEARCH_COARSE_FINE = 1, CP_SEARCH_BANDS = 2 };
+#define CP_BANDS_MAX_FREQ 50000
+#define CP_BANDS_MAX_TRIALS 512
+
 typedef struct {
     double f_min;
     double df;
     int64_t n_freq;
-    int32_t hierarchical;
-    int32_t top_k;
+    int32_t hierarchical;            /* CP_SEARCH_*                                    */
+    int32_t top_k;                   /* coarse-then-fine: peaks refined                */
     double coarse_df;
     double fine_df;
     double fine_halfwidth;
+    int32_t n_bands;                 /* bands method: N_b in [1, 10]                   */
+    int32_t trials_per_band;         /* bands method: N_t in [1, CP_BANDS_MAX_TRIALS]  */
 } cp_freq_grid;
 
 typedef struct {
@@ -142,8 +167,8 @@ cp_status cp_periodogram(cp_plan_t plan, float *out);
  * Section 4.1 for every curve (full grid or coarse-then-fine per the grid).
  * All outputs are HOST arrays of n_curves entries in the caller's curve
  * order; any may be NULL.
- *   best_idx   full grid: k of the best frequency; hierarchical: candidate
- *              index rank*(2J+1) + (j+J)
+ *   best_idx   full grid and bands method: k of the best frequency;
+ *              coarse-then-fine: candidate index rank*(2J+1) + (j+J)
  *   best_freq  FP64 best frequency (1/day); best period = 1/best_freq
  *   best_stat  nCKP at the best frequency
  *   is_periodic  1 if best_stat > th(pSNR bin) of Table tab:th
@@ -164,6 +189,20 @@ cp_status cp_sync(cp_plan_t plan);
  */
 cp_status cp_curve_stats(cp_plan_t plan, float *sigma_y, float *sigma_t, double *ip, float *psnr);
 
+/*
+ * cp_trial_frequencies -- the trial list of the last cp_best_period of a
+ * bands-method plan (Section 3.1), HOST arrays of n_curves x
+ * (n_bands * trials_per_band), row-major in the caller's curve order, band
+ * rank major (entry b * trials_per_band + r = the r-th highest admissible
+ * local maximum of the b-th band in D order); either may be NULL.
+ *   trial_idx   grid index k of the trial frequency, -1 where the band had
+ *               fewer admissible local maxima
+ *   trial_stat  nCKP at that frequency (NaN where trial_idx is -1)
+ * CP_ESTATE for a plan without the bands method or before a search ran.
+ * Synchronous.
+ */
+cp_status cp_trial_frequencies(cp_plan_t plan, int32_t *trial_idx, float *trial_stat);
+
 /* Work and timing of the plan (for throughput and roofline reports). */
 typedef struct {
     int64_t n_curves;
@@ -183,6 +222,10 @@ typedef struct {
                                   /* 2 N^2 n_max per curve and frequency (the upper     */
                                   /* block triangle of the 4 N^2 n_max dense product)   */
     double direct_pair_freq_search; /* pair-frequency evaluations of the direct curves  */
+    float last_bands_kernel_ms;   /* device time of the bands-method kernels, last call */
+    float reserved0;
+    double window_terms_search;   /* bands method: spectral-window terms (band point x  */
+                                  /* grid frequency) of one cp_best_period              */
 } cp_plan_info;
 
 cp_status cp_get_plan_info(cp_plan_t plan, cp_plan_info *info);

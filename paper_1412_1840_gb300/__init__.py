@@ -7,7 +7,8 @@ library cannot be loaded or no CUDA device is present, calls raise.
 
 Entry points carry the C names: ``cp_plan``, ``cp_periodogram``,
 ``cp_best_period``, ``cp_sync``, ``cp_curve_stats``, ``cp_get_plan_info``,
-``cp_destroy``, ``cp_bessel_coefficients``, ``cp_max_points``.  ``Plan`` wraps
+``cp_destroy``, ``cp_bessel_coefficients``, ``cp_max_points``,
+``cp_trial_frequencies``.  ``Plan`` wraps
 a plan handle and keeps the bound input arrays alive.
 """
 from __future__ import annotations
@@ -26,6 +27,8 @@ CP_FORM_DIRECT, CP_FORM_TENSOR = 0, 1
 CP_DTYPE_FP16, CP_DTYPE_BF16 = 0, 1
 CP_SIGMA_T_FIXED, CP_SIGMA_T_PER_CURVE, CP_SIGMA_T_RULE = 0, 1, 2
 CP_MEM_HOST, CP_MEM_DEVICE = 0, 1
+CP_SEARCH_FULL, CP_SEARCH_COARSE_FINE, CP_SEARCH_BANDS = 0, 1, 2
+CP_BANDS_MAX_FREQ, CP_BANDS_MAX_TRIALS = 50000, 512
 
 
 class CpError(RuntimeError):
@@ -37,7 +40,8 @@ class CpError(RuntimeError):
 class cp_freq_grid(ctypes.Structure):
     _fields_ = [("f_min", ctypes.c_double), ("df", ctypes.c_double), ("n_freq", ctypes.c_int64),
                 ("hierarchical", ctypes.c_int32), ("top_k", ctypes.c_int32), ("coarse_df", ctypes.c_double),
-                ("fine_df", ctypes.c_double), ("fine_halfwidth", ctypes.c_double)]
+                ("fine_df", ctypes.c_double), ("fine_halfwidth", ctypes.c_double),
+                ("n_bands", ctypes.c_int32), ("trials_per_band", ctypes.c_int32)]
 
 
 class cp_options(ctypes.Structure):
@@ -53,7 +57,9 @@ class cp_plan_info(ctypes.Structure):
                 ("last_pair_kernel_ms", ctypes.c_float), ("last_step_ms", ctypes.c_float),
                 ("n_sm", ctypes.c_int32), ("max_n", ctypes.c_int32), ("class_curves", ctypes.c_int64 * 5),
                 ("last_tensor_kernel_ms", ctypes.c_float), ("last_direct_kernel_ms", ctypes.c_float),
-                ("tensor_flops_search", ctypes.c_double), ("direct_pair_freq_search", ctypes.c_double)]
+                ("tensor_flops_search", ctypes.c_double), ("direct_pair_freq_search", ctypes.c_double),
+                ("last_bands_kernel_ms", ctypes.c_float), ("reserved0", ctypes.c_float),
+                ("window_terms_search", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -81,6 +87,7 @@ def _load():
         L.cp_sync.argtypes = [vp]
         L.cp_curve_stats.argtypes = [vp, vp, vp, vp, vp]
         L.cp_get_plan_info.argtypes = [vp, ctypes.POINTER(cp_plan_info)]
+        L.cp_trial_frequencies.argtypes = [vp, vp, vp]
         L.cp_destroy.argtypes = [vp]
         L.cp_destroy.restype = None
         L.cp_max_points.restype = i64
@@ -92,7 +99,7 @@ def _load():
         L.cp_status_string.restype = ctypes.c_char_p
         L.cp_last_error.restype = ctypes.c_char_p
         for fn in ("cp_plan", "cp_periodogram", "cp_best_period", "cp_sync", "cp_curve_stats",
-                   "cp_get_plan_info", "cp_bessel_coefficients"):
+                   "cp_get_plan_info", "cp_bessel_coefficients", "cp_trial_frequencies"):
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -142,9 +149,13 @@ def cp_bessel_coefficients(sigma_t: float, n_max: int) -> np.ndarray:
     return out
 
 
-def make_grid(f_min, df, n_freq, hierarchical=False, coarse_df=0.0, top_k=0, fine_df=0.0, fine_halfwidth=0.0):
-    return cp_freq_grid(float(f_min), float(df), int(n_freq), int(bool(hierarchical)), int(top_k),
-                        float(coarse_df), float(fine_df), float(fine_halfwidth))
+def make_grid(f_min, df, n_freq, hierarchical=False, coarse_df=0.0, top_k=0, fine_df=0.0, fine_halfwidth=0.0,
+              bands=False, n_bands=0, trials_per_band=0):
+    """cp_freq_grid; ``bands=True`` selects the bands method of Section 3.1
+    (N_b = n_bands, N_t = trials_per_band) over the uniform grid."""
+    mode = CP_SEARCH_BANDS if bands else (CP_SEARCH_COARSE_FINE if hierarchical else CP_SEARCH_FULL)
+    return cp_freq_grid(float(f_min), float(df), int(n_freq), mode, int(top_k),
+                        float(coarse_df), float(fine_df), float(fine_halfwidth), int(n_bands), int(trials_per_band))
 
 
 class Plan:
@@ -223,6 +234,16 @@ class Plan:
     def sync(self):
         _check(_load().cp_sync(self.handle), "cp_sync")
 
+    def trials(self):
+        """Trial list of the last search of a bands-method plan:
+        ``trial_idx`` [n_curves, n_bands * trials_per_band] grid indices
+        (-1 = none) and ``trial_stat`` (nCKP at each, NaN where none)."""
+        L = int(self.grid.n_bands) * int(self.grid.trials_per_band)
+        idx = np.empty((self.n_curves, L), np.int32)
+        st = np.empty((self.n_curves, L), np.float32)
+        _check(_load().cp_trial_frequencies(self.handle, idx.ctypes.data, st.ctypes.data), "cp_trial_frequencies")
+        return {"trial_idx": idx, "trial_stat": st}
+
     def curve_stats(self):
         n = self.n_curves
         sy = np.empty(n, np.float32); st = np.empty(n, np.float32); ip = np.empty(n, np.float64)
@@ -284,6 +305,10 @@ def cp_destroy(plan: Plan):
     plan.close()
 
 
+def cp_trial_frequencies(plan: Plan):
+    return plan.trials()
+
+
 def cp_best_period_noalloc(times, mags, errs, offsets, grid: cp_freq_grid, sigma_t: float, best_idx=None,
                            best_freq=None, best_stat=None, is_periodic=None, stream=None):
     """Best-period search that allocates no device memory (for callers that
@@ -315,4 +340,5 @@ def cp_best_period_noalloc(times, mags, errs, offsets, grid: cp_freq_grid, sigma
 
 def grid_from(g) -> cp_freq_grid:
     """cp_freq_grid from any object with the synthetic-grid attribute names."""
-    return make_grid(g.f_min, g.df, g.n_freq, g.hierarchical, g.coarse_df, g.top_k, g.fine_df, g.fine_halfwidth)
+    return make_grid(g.f_min, g.df, g.n_freq, g.hierarchical, g.coarse_df, g.top_k, g.fine_df, g.fine_halfwidth,
+                     getattr(g, "bands", False), getattr(g, "n_bands", 0), getattr(g, "trials_per_band", 0))

@@ -97,13 +97,17 @@ struct cp_plan_s {
     int max_n = 0, np2max = 1;
     int64_t kc = 0;   // coarse grid points
     int J = 0;        // fine half-width in steps
+    bool bands = false;          // bands method (Section 3.1)
+    int n_trials = 0;            // n_bands * trials_per_band
+    int ex_lo = 1, ex_hi = 0;    // one-day grid indices (empty when ex_lo > ex_hi)
+    int max_band_points = 0;
     double f_max = 0;
 
     std::vector<int32_t> order;          // slot -> curve
     std::vector<int32_t> fc;             // per curve
     std::vector<int32_t> cls;            // per curve: 0 direct, else tensor harmonics
     int64_t class_count[5] = {0, 0, 0, 0, 0};   // curves per class {direct, 4, 8, 16, 32}
-    std::vector<int64_t> unit_full, unit_coarse, unit_fine, wtile;
+    std::vector<int64_t> unit_full, unit_coarse, unit_fine, unit_list, wtile;
     std::vector<Wave> waves;
     size_t pair_smem = 0;
     int pair_grid = 0;
@@ -124,6 +128,11 @@ struct cp_plan_s {
     float* d_stpc = nullptr;
     int32_t* d_order = nullptr;
     int64_t *d_unit_full = nullptr, *d_unit_coarse = nullptr, *d_unit_fine = nullptr, *d_wtile = nullptr;
+    int64_t* d_unit_list = nullptr;
+    int8_t* d_band_of = nullptr;         // bands method
+    int32_t* d_kept = nullptr;
+    int32_t* d_trials = nullptr;
+    float* d_trial_stat = nullptr;
     float* d_W = nullptr;
     float* d_coarse = nullptr;
     int32_t *d_peaks = nullptr, *d_npeaks = nullptr;
@@ -152,12 +161,15 @@ struct cp_plan_s {
     bool graph_ready = false;
     std::vector<cudaEvent_t> ev_pair;      // 2 per pair launch of a search
     cudaEvent_t ev_step0 = nullptr, ev_step1 = nullptr;
-    float last_pair_ms = 0.f, last_step_ms = 0.f, last_tensor_ms = 0.f, last_direct_ms = 0.f;
+    cudaEvent_t ev_bands0 = nullptr, ev_bands1 = nullptr;
+    float last_pair_ms = 0.f, last_step_ms = 0.f, last_tensor_ms = 0.f, last_direct_ms = 0.f, last_bands_ms = 0.f;
+    double window_terms = 0;
     std::vector<int> ev_cls;               // class of each pair launch (0 direct)
     double tensor_flops = 0, direct_pf = 0;
     int64_t launches_per_search = 0;
     double pf_full = 0, pf_search = 0;
     bool ran = false;
+    bool searched = false;    // a best-period search completed (trial list valid)
     bool capturing = false;   // inside build_graph's stream capture
 };
 
@@ -166,6 +178,7 @@ namespace {
 inline unsigned long long* status_word(cp_plan_t p) { return p->d_u64; }
 inline unsigned long long* best_keys(cp_plan_t p) { return p->d_u64 + 1; }
 inline unsigned long long* queue_word(cp_plan_t p, int i) { return p->d_u64 + 1 + p->n_curves + i; }
+constexpr int kQueuesPerWave = 4;   // one work counter per (wave, stage)
 
 constexpr int kCoefStride = 32;   // a_1..a_32 stored per curve (largest class)
 
@@ -310,7 +323,7 @@ cp_status enqueue_stats(cp_plan_t p, cudaStream_t s)
     a.df = p->grid.df;
     a.coarse_df = p->grid.coarse_df;
     a.fine_df = p->grid.fine_df;
-    a.hierarchical = p->grid.hierarchical ? 1 : 0;
+    a.hierarchical = p->grid.hierarchical == CP_SEARCH_COARSE_FINE ? 1 : 0;   // coarse / fine phase steps
     a.sigma_t_mode = p->opt.sigma_t_mode;
     a.sigma_t = p->opt.sigma_t;
     a.alpha = p->opt.alpha;
@@ -347,9 +360,18 @@ PairArgs pair_args(cp_plan_t p, int stage, int w, float* out)
     a.out_ld = p->grid.n_freq;
     a.coarse_out = p->d_coarse;
     a.best_key = best_keys(p);
-    a.queue = queue_word(p, 3 * w + stage);
+    a.queue = queue_word(p, kQueuesPerWave * w + stage);
     const std::vector<int64_t>* us;
-    if (stage == kStageFull) {
+    if (stage == kStageList) {
+        a.unit_start = p->d_unit_list;
+        a.ph_step = p->d_ph_full;
+        a.n_freq = p->grid.n_freq;
+        a.step = p->grid.df;
+        a.trials = p->d_trials;
+        a.n_trials = p->n_trials;
+        a.trial_stat = p->d_trial_stat;
+        us = &p->unit_list;
+    } else if (stage == kStageFull) {
         a.unit_start = p->d_unit_full;
         a.ph_step = p->d_ph_full;
         a.n_freq = p->grid.n_freq;
@@ -442,6 +464,9 @@ TensorArgs tensor_args(const PairArgs& d, cp_plan_t p)
     t.status = reinterpret_cast<int*>(status_word(p));
     t.wait_limit = p->wait_limit;
     t.ctas_per_unit = 1;
+    t.trials = d.trials;
+    t.n_trials = d.n_trials;
+    t.trial_stat = d.trial_stat;
     return t;
 }
 
@@ -472,10 +497,40 @@ cp_status enqueue_search(cp_plan_t p, cudaStream_t s)
     CP_CUDA(cudaEventRecordWithFlags(p->ev_step0, s, rec_flags(p)));
     if ((st = enqueue_inputs(p, s)) != CP_OK) return st;
     if ((st = enqueue_stats(p, s)) != CP_OK) return st;
+    if (p->bands) {
+        CP_CUDA(cudaEventRecordWithFlags(p->ev_bands0, s, rec_flags(p)));
+        BandsArgs b{};
+        b.times = p->host_inputs ? p->d_times : p->times;
+        b.mags = p->host_inputs ? p->d_mags : p->mags;
+        b.cp = p->d_cp;
+        b.band_of = p->d_band_of;
+        b.kept = p->d_kept;
+        b.n_bands = p->grid.n_bands;
+        b.np2max = p->np2max;
+        CP_CUDA(launch_bands(b, (int)p->n_curves, s));
+        WindowArgs wa{};
+        wa.cp = p->d_cp;
+        wa.band_of = p->d_band_of;
+        wa.kept = p->d_kept;
+        wa.ph_base = p->d_ph_base;
+        wa.ph_step = p->d_ph_full;
+        wa.trials = p->d_trials;
+        wa.n_curves = (int)p->n_curves;
+        wa.n_bands = p->grid.n_bands;
+        wa.n_t = p->grid.trials_per_band;
+        wa.n_freq = (int)p->grid.n_freq;
+        wa.ex_lo = p->ex_lo;
+        wa.ex_hi = p->ex_hi;
+        wa.max_band_points = p->max_band_points;
+        CP_CUDA(launch_window(wa, s));
+        CP_CUDA(cudaEventRecordWithFlags(p->ev_bands1, s, rec_flags(p)));
+    }
     int ev = 0;
     for (int w = 0; w < (int)p->waves.size(); w++) {
         if ((st = enqueue_wave_w(p, w, s)) != CP_OK) return st;
-        if (!p->grid.hierarchical) {
+        if (p->bands) {
+            if ((st = enqueue_pair(p, kStageList, w, nullptr, s, &ev)) != CP_OK) return st;
+        } else if (!p->grid.hierarchical) {
             if ((st = enqueue_pair(p, kStageFull, w, nullptr, s, &ev)) != CP_OK) return st;
         } else {
             if ((st = enqueue_pair(p, kStageCoarse, w, nullptr, s, &ev)) != CP_OK) return st;
@@ -497,8 +552,10 @@ cp_status enqueue_search(cp_plan_t p, cudaStream_t s)
     f.best_key = best_keys(p);
     f.peaks = p->d_peaks;
     f.n_curves = (int)p->n_curves;
-    f.hierarchical = p->grid.hierarchical ? 1 : 0;
+    f.hierarchical = p->grid.hierarchical;
     f.top_k = p->grid.top_k;
+    f.trials = p->d_trials;
+    f.n_trials = p->n_trials;
     f.fine_half = p->J;
     f.f_min = p->grid.f_min;
     f.df = p->grid.df;
@@ -557,6 +614,10 @@ cp_status read_timings(cp_plan_t p)
     float ms = 0.f;
     CP_CUDA(cudaEventElapsedTime(&ms, p->ev_step0, p->ev_step1));
     p->last_step_ms = ms;
+    if (p->bands) {
+        CP_CUDA(cudaEventElapsedTime(&ms, p->ev_bands0, p->ev_bands1));
+        p->last_bands_ms = ms;
+    }
     return CP_OK;
 }
 
@@ -609,6 +670,8 @@ void cp_destroy(cp_plan_t p)
     for (cudaEvent_t e : p->ev_pair) cudaEventDestroy(e);
     if (p->ev_step0) cudaEventDestroy(p->ev_step0);
     if (p->ev_step1) cudaEventDestroy(p->ev_step1);
+    if (p->ev_bands0) cudaEventDestroy(p->ev_bands0);
+    if (p->ev_bands1) cudaEventDestroy(p->ev_bands1);
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->dblock) cudaFree(p->dblock);
     if (p->hblock) cudaFreeHost(p->hblock);
@@ -655,7 +718,35 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     if (g.n_freq < 1 || g.n_freq > ((int64_t)1 << 31) - 1)
         return fail(CP_EINVAL, "cp_plan: n_freq must be in [1, 2^31)");
     p->f_max = g.f_min + (double)(g.n_freq - 1) * g.df;
-    if (g.hierarchical) {
+    if (g.hierarchical < CP_SEARCH_FULL || g.hierarchical > CP_SEARCH_BANDS)
+        return fail(CP_EINVAL, "cp_plan: hierarchical must be CP_SEARCH_FULL, _COARSE_FINE or _BANDS");
+    if (g.hierarchical == CP_SEARCH_BANDS) {
+        if (g.n_bands < 1 || g.n_bands > 10)
+            return fail(CP_EINVAL, "cp_plan: n_bands must be in [1, 10]");
+        if (g.trials_per_band < 1 || g.trials_per_band > kBandsMaxTrials)
+            return fail(CP_EINVAL, "cp_plan: trials_per_band must be in [1, " + std::to_string(kBandsMaxTrials) + "]");
+        if (g.n_freq > kBandsMaxFreq)
+            return fail(CP_EUNSUPPORTED, "cp_plan: the bands method holds each spectral window in shared memory; "
+                                         "n_freq must be <= " + std::to_string(kBandsMaxFreq));
+        p->bands = true;
+        p->n_trials = g.n_bands * g.trials_per_band;
+        // grid indices of the one-day frequencies |1/f - 1| < 1e-4 (a contiguous range; the
+        // test is evaluated per index with the FP64 expressions of the search itself)
+        const double klo = std::floor((1.0 / 1.0001 - g.f_min) / g.df) - 2.0;
+        const double khi = std::ceil((1.0 / 0.9999 - g.f_min) / g.df) + 2.0;
+        if (khi >= 0.0 && klo <= (double)(g.n_freq - 1)) {
+            const int64_t a0 = std::max<int64_t>(0, (int64_t)klo), a1 = std::min<int64_t>(g.n_freq - 1, (int64_t)khi);
+            for (int64_t k = a0; k <= a1; k++) {
+                const double prod = (double)k * g.df;
+                const double f = g.f_min + prod;
+                if (f > 0.0 && std::fabs(1.0 / f - 1.0) < 1e-4) {
+                    if (p->ex_lo > p->ex_hi) p->ex_lo = p->ex_hi = (int)k;
+                    p->ex_lo = std::min(p->ex_lo, (int)k);
+                    p->ex_hi = std::max(p->ex_hi, (int)k);
+                }
+            }
+        }
+    } else if (g.hierarchical) {
         if (!(g.coarse_df > 0.0 && std::isfinite(g.coarse_df) && g.fine_df > 0.0 && std::isfinite(g.fine_df) &&
               g.fine_halfwidth >= 0.0 && std::isfinite(g.fine_halfwidth)))
             return fail(CP_EINVAL, "cp_plan: hierarchical grid needs coarse_df > 0, fine_df > 0, fine_halfwidth >= 0");
@@ -683,6 +774,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         max_n = std::max(max_n, (int)n);
         p->fc[c] = fc_for((int)n);
     }
+    p->max_band_points = (max_n + 9) / 10;   // a band holds at most ceil(N/10) samples
     p->n_points = offsets[n_curves];
     p->max_n = max_n;
     while (p->np2max < max_n) p->np2max <<= 1;
@@ -750,6 +842,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     p->unit_full.assign(n_curves + 1, 0);
     p->unit_coarse.assign(n_curves + 1, 0);
     p->unit_fine.assign(n_curves + 1, 0);
+    p->unit_list.assign(n_curves + 1, 0);
     p->wtile.assign(n_curves + 1, 0);
     double pf_full = 0, pf_search = 0;
     size_t smem = 0;
@@ -759,7 +852,11 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         const int f = p->cls[c] ? 128 / p->cls[c] : p->fc[c];
         const double pairs = 0.5 * (double)n * (double)(n - 1);
         p->unit_full[s + 1] = p->unit_full[s] + (g.n_freq + f - 1) / f;
-        if (g.hierarchical) {
+        p->unit_list[s + 1] = p->unit_list[s] + (p->n_trials + f - 1) / f;
+        if (p->bands) {
+            pf_search += pairs * (double)p->n_trials;
+            p->window_terms += (double)n * (double)g.n_freq * (double)g.n_bands / 10.0;
+        } else if (g.hierarchical) {
             p->unit_coarse[s + 1] = p->unit_coarse[s] + (p->kc + f - 1) / f;
             p->unit_fine[s + 1] = p->unit_fine[s] + (int64_t)g.top_k * ((2 * p->J + 1 + f - 1) / f);
             pf_search += pairs * (double)(p->kc + (int64_t)g.top_k * (2 * p->J + 1));
@@ -768,7 +865,9 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         }
         pf_full += pairs * (double)g.n_freq;
         {
-            const double kk = g.hierarchical ? (double)(p->kc + (int64_t)g.top_k * (2 * p->J + 1)) : (double)g.n_freq;
+            const double kk = p->bands ? (double)p->n_trials
+                              : g.hierarchical ? (double)(p->kc + (int64_t)g.top_k * (2 * p->J + 1))
+                                               : (double)g.n_freq;
             if (p->cls[c]) p->tensor_flops += 2.0 * (double)n * (double)n * (double)p->cls[c] * kk;
             else p->direct_pf += pairs * kk;
         }
@@ -812,10 +911,11 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
 
     // device allocation (one block)
     const int64_t np = p->n_points, nc = n_curves;
-    const int nq = 3 * (int)p->waves.size();
+    const int nq = kQueuesPerWave * (int)p->waves.size();
     p->n_u64 = 1 + nc + nq;
     struct Part { void** dst; size_t bytes; };
-    const bool hier = g.hierarchical != 0;
+    const bool hier = g.hierarchical == CP_SEARCH_COARSE_FINE;
+    const bool bnd = p->bands;
     std::vector<Part> parts = {
         {(void**)&p->d_times, p->host_inputs ? np * sizeof(double) : 0},
         {(void**)&p->d_mags, p->host_inputs ? np * sizeof(float) : 0},
@@ -832,6 +932,11 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         {(void**)&p->d_unit_coarse, (nc + 1) * sizeof(int64_t)},
         {(void**)&p->d_unit_fine, (nc + 1) * sizeof(int64_t)},
         {(void**)&p->d_wtile, (nc + 1) * sizeof(int64_t)},
+        {(void**)&p->d_unit_list, bnd ? (nc + 1) * sizeof(int64_t) : 0},
+        {(void**)&p->d_band_of, bnd ? (size_t)np : 0},
+        {(void**)&p->d_kept, bnd ? (size_t)nc * g.n_bands * sizeof(int32_t) : 0},
+        {(void**)&p->d_trials, bnd ? (size_t)nc * p->n_trials * sizeof(int32_t) : 0},
+        {(void**)&p->d_trial_stat, bnd ? (size_t)nc * p->n_trials * sizeof(float) : 0},
         {(void**)&p->d_W, (size_t)max_tiles32 * tile32_bytes},
         {(void**)&p->d_W16, (size_t)max_tiles16 * tile16_bytes},
         {(void**)&p->d_coef, p->tensor ? (size_t)nc * kCoefStride * sizeof(float) : 0},
@@ -842,7 +947,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         {(void**)&p->d_res_idx, nc * sizeof(int64_t)},
         {(void**)&p->d_res_freq, nc * sizeof(double)},
         {(void**)&p->d_res_stat, nc * sizeof(float)},
-        {(void**)&p->d_res_per, nc},
+        {(void**)&p->d_res_per, (size_t)nc},
         {(void**)&p->d_res_psnr, nc * sizeof(float)},
     };
     size_t total = 0;
@@ -894,6 +999,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     CP_CUDA(cudaMemcpy(p->d_unit_coarse, p->unit_coarse.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
     CP_CUDA(cudaMemcpy(p->d_unit_fine, p->unit_fine.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
     CP_CUDA(cudaMemcpy(p->d_wtile, p->wtile.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (bnd)
+        CP_CUDA(cudaMemcpy(p->d_unit_list, p->unit_list.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
     if (opt.sigma_t_mode == CP_SIGMA_T_PER_CURVE) {
         for (int64_t c = 0; c < nc; c++)
             if (!(opt.sigma_t_per_curve[c] > 0.f && std::isfinite(opt.sigma_t_per_curve[c])))
@@ -904,6 +1011,14 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
 
     // launch geometry of the persistent pair kernel
     CP_CUDA(prepare_kernels(p->np2max, p->pair_smem));
+    if (bnd) {
+        int optin = 0;
+        CP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+        if (window_smem_bytes((int)g.n_freq, p->max_band_points) + 4096 > (size_t)optin)
+            return fail(CP_EUNSUPPORTED, "cp_plan: spectral window of " + std::to_string(g.n_freq) +
+                                             " frequencies does not fit in shared memory");
+        CP_CUDA(prepare_bands_kernels(p->np2max, (int)g.n_freq, p->max_band_points));
+    }
     for (int nm : {4, 8, 16, 32})
         if (p->class_count[class_rank(nm)]) CP_CUDA(prepare_tensor_kernel(nm));   // one CTA per SM
     {
@@ -913,15 +1028,19 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     }
 
     // events
-    const int pair_launches = (int)p->waves.size() * (g.hierarchical ? 2 : 1);
+    const int pair_launches = (int)p->waves.size() * (hier ? 2 : 1);
     p->ev_pair.resize(2 * pair_launches);
     p->ev_cls.assign(pair_launches, 0);
     for (auto& e : p->ev_pair) CP_CUDA(cudaEventCreate(&e));
     CP_CUDA(cudaEventCreate(&p->ev_step0));
     CP_CUDA(cudaEventCreate(&p->ev_step1));
+    if (bnd) {
+        CP_CUDA(cudaEventCreate(&p->ev_bands0));
+        CP_CUDA(cudaEventCreate(&p->ev_bands1));
+    }
     p->launches_per_search =
-        2 /* zero, stats */ + (p->tensor ? 1 : 0) /* harmonic coefficients */ +
-        (int64_t)p->waves.size() * (g.hierarchical ? 4 : 2) + 1 /* finalize */;
+        2 /* zero, stats */ + (p->tensor ? 1 : 0) /* harmonic coefficients */ + (bnd ? 2 : 0) /* bands, window */ +
+        (int64_t)p->waves.size() * (hier ? 4 : 2) + 1 /* finalize */;
     return CP_OK;
 }
 
@@ -1007,6 +1126,7 @@ static cp_status best_period_impl(cp_plan_t p, int64_t* best_idx, double* best_f
     }
     CP_CUDA(cudaStreamSynchronize(p->stream));
     p->ran = true;
+    p->searched = true;
     if ((st = read_timings(p)) != CP_OK) {
         cudaSetDevice(prev);
         return st;
@@ -1041,6 +1161,27 @@ static cp_status curve_stats_impl(cp_plan_t p, float* sigma_y, float* sigma_t, d
     return CP_OK;
 }
 
+static cp_status trials_impl(cp_plan_t p, int32_t* trial_idx, float* trial_stat)
+{
+    if (!p) return fail(CP_EINVAL, "cp_trial_frequencies: NULL plan");
+    if (!p->bands) return fail(CP_ESTATE, "cp_trial_frequencies: the plan does not use the bands method");
+    if (!p->searched) return fail(CP_ESTATE, "cp_trial_frequencies: no best-period search has run on this plan");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    CP_CUDA(cudaSetDevice(p->device));
+    CP_CUDA(cudaStreamSynchronize(p->stream));
+    const size_t cnt = (size_t)p->n_curves * (size_t)p->n_trials;
+    if (trial_idx) CP_CUDA(cudaMemcpy(trial_idx, p->d_trials, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (trial_stat) CP_CUDA(cudaMemcpy(trial_stat, p->d_trial_stat, cnt * sizeof(float), cudaMemcpyDeviceToHost));
+    cudaSetDevice(prev);
+    return CP_OK;
+}
+
+cp_status cp_trial_frequencies(cp_plan_t p, int32_t* trial_idx, float* trial_stat)
+{
+    return finish(trials_impl(p, trial_idx, trial_stat), "cp_trial_frequencies");
+}
+
 cp_status cp_periodogram(cp_plan_t p, float* out) { return finish(periodogram_impl(p, out), "cp_periodogram"); }
 
 cp_status cp_sync(cp_plan_t p) { return finish(sync_impl(p), "cp_sync"); }
@@ -1073,6 +1214,9 @@ cp_status cp_get_plan_info(cp_plan_t p, cp_plan_info* info)
     info->last_direct_kernel_ms = p->last_direct_ms;
     info->tensor_flops_search = p->tensor_flops;
     info->direct_pair_freq_search = p->direct_pf;
+    info->last_bands_kernel_ms = p->last_bands_ms;
+    info->reserved0 = 0.f;
+    info->window_terms_search = p->window_terms;
     return CP_OK;
 }
 

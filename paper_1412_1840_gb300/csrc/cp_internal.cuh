@@ -47,7 +47,9 @@ struct CurveParams {
 };
 
 // Search stages.
-enum Stage : int { kStageFull = 0, kStageCoarse = 1, kStageFine = 2 };
+// kStageList evaluates an explicit per-curve list of grid indices (the trial
+// frequencies of the bands method).
+enum Stage : int { kStageFull = 0, kStageCoarse = 1, kStageFine = 2, kStageList = 3 };
 
 // Direct-form pair tiling: a warp owns a 32 x 32 tile of (row i, col j)
 // pairs of the upper block triangle; lane (a, b) = (lane / 8, lane % 8)
@@ -88,6 +90,9 @@ struct PairArgs {
     float* coarse_out;           // coarse stage: [n_curves * n_freq]
     unsigned long long* best_key;// [n_curves]
     unsigned long long* queue;   // work counter of this (stage, wave)
+    const int32_t* trials;       // list stage: [n_curves * n_trials] grid indices, -1 = none
+    int32_t n_trials;
+    float* trial_stat;           // list stage: nCKP per trial (may be null)
 };
 
 struct StatsArgs {
@@ -135,10 +140,12 @@ struct FinalArgs {
     const unsigned long long* best_key;
     const int32_t* peaks;
     int n_curves;
-    int hierarchical;
+    int hierarchical;             // CP_SEARCH_*
     int top_k;
     int fine_half;
     double f_min, df, coarse_df, fine_df;
+    const int32_t* trials;        // bands method: best key index -> grid index
+    int32_t n_trials;
     int64_t* best_idx;
     double* best_freq;
     float* best_stat;
@@ -188,7 +195,43 @@ struct TensorArgs {
     int* status;
     uint32_t wait_limit;          // polls before a wait gives up (CP_ETIMEOUT)
     int32_t ctas_per_unit;        // 1 (one CTA per unit)
+    const int32_t* trials;        // list stage (as in PairArgs)
+    int32_t n_trials;
+    float* trial_stat;
 };
+
+// Bands method, Section 3.1 (cp_bands.cu).
+constexpr int kBandsMaxFreq = CP_BANDS_MAX_FREQ;
+constexpr int kBandsMaxTrials = CP_BANDS_MAX_TRIALS;
+
+struct BandsArgs {
+    const double* times;
+    const float* mags;
+    const CurveParams* cp;
+    int8_t* band_of;              // [n_points] band 0..9 of every sample
+    int32_t* kept;                // [n_curves * n_bands] bands in D order
+    int n_bands;
+    int np2max;
+};
+
+struct WindowArgs {
+    const CurveParams* cp;
+    const int8_t* band_of;
+    const int32_t* kept;
+    const uint64_t* ph_base;      // frac(f_min (t - t0)) in 2^-64 turns
+    const uint64_t* ph_step;      // frac(df (t - t0))
+    int32_t* trials;              // [n_curves * n_bands * n_t]
+    int n_curves, n_bands, n_t;
+    int n_freq;
+    int ex_lo, ex_hi;             // one-day grid indices [ex_lo, ex_hi] (ex_lo > ex_hi: none)
+    int max_band_points;
+};
+
+size_t bands_smem_bytes(int np2max);
+size_t window_smem_bytes(int n_freq, int max_band_points);
+cudaError_t prepare_bands_kernels(int np2max, int n_freq, int max_band_points);
+cudaError_t launch_bands(const BandsArgs& a, int n_curves, cudaStream_t s);
+cudaError_t launch_window(const WindowArgs& a, cudaStream_t s);
 
 size_t tensor_smem_bytes();
 int tensor_tiles_of(int n);
@@ -262,6 +305,23 @@ __device__ __forceinline__ void sincospi_turns(uint32_t U, float& s, float& c)
     // x + 1/2: sin -> cos, cos -> -sin
     s = n ? cx : sx;
     c = n ? -sx : cx;
+}
+
+// sin(2 pi x), cos(2 pi x) for x = U / 2^32, exact quadrant handling.
+__device__ __forceinline__ void sincos2pi_turns(uint32_t U, float& s, float& c)
+{
+    const uint32_t q = ((U + 0x20000000u) >> 30) & 3u;      // nearest quarter turn
+    const int32_t r = (int32_t)(U - (q << 30));              // [-2^29, 2^29)
+    // reuse the pi-polynomial on the doubled residual: sin(2 pi r') = sin(pi (2 r'))
+    const uint32_t U2 = (uint32_t)(r * 2);                    // 2r' in turns of pi, |.| <= 1/4
+    float sx, cx;
+    sincospi_turns(U2, sx, cx);                               // n = 0 branch: exact for |x| <= 1/4
+    switch (q) {
+    case 0: s = sx; c = cx; break;
+    case 1: s = cx; c = -sx; break;
+    case 2: s = -sx; c = -cx; break;
+    default: s = -cx; c = sx; break;
+    }
 }
 
 __device__ __forceinline__ float ex2_approx(float x)

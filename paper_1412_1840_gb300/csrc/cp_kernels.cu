@@ -8,6 +8,7 @@
 //                  work units: the N(N-1)/2 interactions of Section 8 per
 //                  trial frequency, FP32 with packed f32x2 arithmetic
 //   k_topk         coarse-grid local maxima for the coarse-then-fine search
+//                  (the bands method of Section 3.1 is in cp_bands.cu)
 //   k_finalize     best frequency, nCKP and Table tab:th discriminator
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -298,10 +299,14 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
             peak_mult = (uint64_t)a.peaks[(int64_t)c * a.top_k + peak];
             kfirst = -a.fine_half + (long long)sub * fc;
             count = (int)min((long long)fc, (long long)a.fine_half - kfirst + 1);
+        } else if (a.stage == kStageList) {
+            kfirst = chunk * fc;     // first list position
+            count = (int)min((long long)fc, (long long)a.n_trials - kfirst);
         } else {
             kfirst = chunk * fc;
             count = (int)min((long long)fc, a.n_freq - kfirst);
         }
+        const int32_t* tl = a.trials + (int64_t)c * a.n_trials;   // list stage only
 
         // trig table: SC[fp][i] = {(s_f, s_f'), (c_f, c_f')} * sqrt(beta), NS[fp][i] = -(s_f, s_f')
         ulonglong2* SC = reinterpret_cast<ulonglong2*>(smem);
@@ -314,10 +319,21 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
             if (i < n) {
                 const uint64_t st = a.ph_step[off + i];
                 uint64_t ph = a.ph_base[off + i] + (uint64_t)(kfirst + 2 * fp) * st;
-                if (a.stage == kStageFine) ph += peak_mult * a.ph_coarse[off + i];
+                uint64_t ph1 = ph + st;
+                if (a.stage == kStageFine) {
+                    ph += peak_mult * a.ph_coarse[off + i];
+                    ph1 = ph + st;
+                } else if (a.stage == kStageList) {
+                    // grid indices of list positions kfirst + 2 fp (+1); a missing entry evaluates k = 0
+                    const long long q0 = kfirst + 2 * fp;
+                    const int k0 = q0 < a.n_trials ? max(tl[q0], 0) : 0;
+                    const int k1 = q0 + 1 < a.n_trials ? max(tl[q0 + 1], 0) : 0;
+                    ph = a.ph_base[off + i] + (uint64_t)k0 * st;
+                    ph1 = a.ph_base[off + i] + (uint64_t)k1 * st;
+                }
                 float s0, c0, s1, c1;
                 sincospi_turns((uint32_t)(ph >> 32), s0, c0);
-                sincospi_turns((uint32_t)((ph + st) >> 32), s1, c1);
+                sincospi_turns((uint32_t)(ph1 >> 32), s1, c1);
                 s0 *= ts; c0 *= ts; s1 *= ts; c1 *= ts;
                 v = make_ulonglong2(pk(s0, s1), pk(c0, c1));
                 ns = pk(-s0, -s1);
@@ -430,6 +446,10 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
                     key = make_key(v, (uint32_t)kk);
                 } else if (a.stage == kStageCoarse) {
                     a.coarse_out[(int64_t)c * a.n_freq + kk] = v;
+                } else if (a.stage == kStageList) {
+                    const bool valid = tl[kk] >= 0;
+                    if (a.trial_stat) a.trial_stat[(int64_t)c * a.n_trials + kk] = valid ? v : __int_as_float(0x7fc00000);
+                    if (valid) key = make_key(v, (uint32_t)kk);
                 } else {
                     const double fpk = a.f_min + (double)peak_mult * a.coarse_df;
                     const double f = fpk + (double)kk * a.step;
@@ -509,16 +529,20 @@ __global__ void k_finalize(const FinalArgs a)
     const float v = from_orderable((uint32_t)(key >> 32));
     const uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
     double f;
-    if (a.hierarchical) {
+    uint32_t kout = idx;
+    if (a.hierarchical == CP_SEARCH_BANDS) {
+        kout = (uint32_t)a.trials[(int64_t)c * a.n_trials + idx];   // list position -> grid index
+        f = __dadd_rn(a.f_min, __dmul_rn((double)kout, a.df));
+    } else if (a.hierarchical) {
         const int W = 2 * a.fine_half + 1;
         const int p = (int)(idx / (uint32_t)W);
         const int j = (int)(idx % (uint32_t)W) - a.fine_half;
-        const double fpk = a.f_min + (double)a.peaks[(int64_t)c * a.top_k + p] * a.coarse_df;
-        f = fpk + (double)j * a.fine_df;
+        const double fpk = __dadd_rn(a.f_min, __dmul_rn((double)a.peaks[(int64_t)c * a.top_k + p], a.coarse_df));
+        f = __dadd_rn(fpk, __dmul_rn((double)j, a.fine_df));
     } else {
-        f = a.f_min + (double)idx * a.df;
+        f = __dadd_rn(a.f_min, __dmul_rn((double)idx, a.df));
     }
-    a.best_idx[c] = (int64_t)idx;
+    a.best_idx[c] = (int64_t)kout;
     a.best_freq[c] = f;
     a.best_stat[c] = v;
     a.is_periodic[c] = v > a.cp[c].th ? 1 : 0;

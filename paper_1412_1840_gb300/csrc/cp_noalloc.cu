@@ -96,6 +96,10 @@ extern "C" cp_status cp_best_period_noalloc(const double* times, const float* ma
     const double f_max = g.f_min + (double)(g.n_freq - 1) * g.df;
     int64_t kc = 0;
     int J = 0;
+    if (g.hierarchical == CP_SEARCH_BANDS)
+        return nfail(CP_EUNSUPPORTED, "cp_best_period_noalloc: the bands method needs a plan (cp_plan)");
+    if (g.hierarchical != CP_SEARCH_FULL && g.hierarchical != CP_SEARCH_COARSE_FINE)
+        return nfail(CP_EINVAL, "cp_best_period_noalloc: bad search mode");
     if (g.hierarchical) {
         if (!(g.coarse_df > 0.0 && g.fine_df > 0.0 && g.fine_halfwidth >= 0.0) || g.top_k < 1 || g.top_k > 1024)
             return nfail(CP_EINVAL, "cp_best_period_noalloc: bad hierarchical grid");

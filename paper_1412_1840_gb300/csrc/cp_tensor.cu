@@ -36,7 +36,6 @@ constexpr int kTcB = 32768;            // 256 x 64 x 2 B
 constexpr int kTcStageBytes = 2 * kTcA + kTcB;   // W' tiles of two M-tiles + one Z tile
 constexpr int kTcCols = 256;           // columns per unit
 constexpr int kTcProducers = 256;      // warps 6..13
-constexpr uint32_t kWaitLimit = 1u << 26;
 constexpr int kTcTablePoints = 1024;   // per-unit phase table in shared memory (producers)
 
 __host__ __device__ inline int tc_mtiles(int n) { return (n + 127) / 128; }
@@ -52,23 +51,6 @@ __host__ __device__ inline int tc_tile_index(int I, int J, int nkc)
 {
     // tiles stored I-major: sum_{I' < I} (nkc - 2 I') + (J - 2 I)
     return I * nkc - I * (I - 1) + (J - 2 * I);
-}
-
-// sin(2 pi x), cos(2 pi x) for x = U / 2^32, exact quadrant handling.
-__device__ __forceinline__ void sincos2pi_turns(uint32_t U, float& s, float& c)
-{
-    const uint32_t q = ((U + 0x20000000u) >> 30) & 3u;      // nearest quarter turn
-    const int32_t r = (int32_t)(U - (q << 30));              // [-2^29, 2^29)
-    // reuse the pi-polynomial on the doubled residual: sin(2 pi r') = sin(pi (2 r'))
-    const uint32_t U2 = (uint32_t)(r * 2);                    // 2r' in turns of pi, |.| <= 1/4
-    float sx, cx;
-    sincospi_turns(U2, sx, cx);                               // n = 0 branch: exact for |x| <= 1/4
-    switch (q) {
-    case 0: s = sx; c = cx; break;
-    case 1: s = cx; c = -sx; break;
-    case 2: s = -sx; c = -cx; break;
-    default: s = -cx; c = sx; break;
-    }
 }
 
 __device__ __forceinline__ uint16_t to16(float v, bool bf)
@@ -236,6 +218,9 @@ __device__ __forceinline__ TcUnit tc_decode(const TensorArgs& a, int64_t u)
         U.peak_mult = U.empty ? 0 : (uint64_t)a.peaks[(int64_t)U.c * a.top_k + U.peak];
         U.kfirst = -a.fine_half + (int64_t)sub * ft;
         U.count = (int)min((int64_t)ft, (int64_t)a.fine_half - U.kfirst + 1);
+    } else if (a.stage == kStageList) {
+        U.kfirst = chunk * ft;       // first list position
+        U.count = (int)min((int64_t)ft, (int64_t)a.n_trials - U.kfirst);
     } else {
         U.kfirst = chunk * ft;
         U.count = (int)min((int64_t)ft, a.n_freq - U.kfirst);
@@ -243,10 +228,27 @@ __device__ __forceinline__ TcUnit tc_decode(const TensorArgs& a, int64_t u)
     return U;
 }
 
-__device__ __forceinline__ uint32_t tc_phase_u32(const TensorArgs& a, const TcUnit& U, int64_t off, int i, int f)
+// Frequency multiplier of the unit's f-th frequency relative to the phase
+// table base: f for the uniform stages (base = ph_base + kfirst * step), the
+// grid index of list position kfirst + f for the list stage (base = ph_base;
+// a missing entry evaluates k = 0 and is never emitted).
+__device__ __forceinline__ uint64_t tc_mult(const TensorArgs& a, const TcUnit& U, int f)
+{
+    if (a.stage != kStageList) return (uint64_t)f;
+    const int64_t q = U.kfirst + f;
+    return q < a.n_trials ? (uint64_t)max(a.trials[(int64_t)U.c * a.n_trials + q], 0) : 0ull;
+}
+
+__device__ __forceinline__ uint64_t tc_base_mult(const TensorArgs& a, const TcUnit& U)
+{
+    return a.stage == kStageList ? 0ull : (uint64_t)U.kfirst;
+}
+
+__device__ __forceinline__ uint32_t tc_phase_u32(const TensorArgs& a, const TcUnit& U, int64_t off, int i,
+                                                 uint64_t mult)
 {
     const uint64_t st = a.ph_step[off + i];
-    uint64_t ph = a.ph_base[off + i] + (uint64_t)(U.kfirst + f) * st;
+    uint64_t ph = a.ph_base[off + i] + (tc_base_mult(a, U) + mult) * st;
     if (a.stage == kStageFine) ph += U.peak_mult * a.ph_coarse[off + i];
     return (uint32_t)(ph >> 32);
 }
@@ -380,6 +382,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
         const int lg = warp & 3;                      // TMEM lane group this warp may access
         const int row = lg * 32 + lane;
         const int ew = warp - 2;                      // epilogue warp index 0..3
+        const bool list = a.stage == kStageList;      // explicit frequencies: no rotation shortcut
         uint32_t m = 0;
         bool ok = true;
         for (int64_t u = a.unit_begin + blockIdx.x / a.ctas_per_unit; ok && u < a.unit_end; u += gridDim.x) {
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                     live[h] = i < U.n;
                     if (live[h]) {
                         pstep[h] = a.ph_step[off + i];
-                        ph0[h] = a.ph_base[off + i] + (uint64_t)U.kfirst * pstep[h];
+                        ph0[h] = a.ph_base[off + i] + tc_base_mult(a, U) * pstep[h];
                         if (a.stage == kStageFine) ph0[h] += U.peak_mult * a.ph_coarse[off + i];
                     }
                 }
@@ -422,8 +425,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
 #pragma unroll
                         for (int f = 0; f < FT; f++) {
                             if (live[h]) {
-                                if ((f & 1) == 0) {
-                                    sincos2pi_turns((uint32_t)((ph0[h] + (uint64_t)f * pstep[h]) >> 32), s1, c1);
+                                if ((f & 1) == 0 || list) {
+                                    sincos2pi_turns((uint32_t)((ph0[h] + tc_mult(a, U, f) * pstep[h]) >> 32), s1, c1);
                                 } else {
                                     const float cn = fmaf(c1, cr, -s1 * sr), sn = fmaf(s1, cr, c1 * sr);
                                     c1 = cn;
@@ -472,6 +475,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                         key = make_key(v, (uint32_t)kk);
                     } else if (a.stage == kStageCoarse) {
                         a.coarse_out[(int64_t)U.c * a.n_freq + kk] = v;
+                    } else if (list) {
+                        const bool valid = a.trials[(int64_t)U.c * a.n_trials + kk] >= 0;
+                        if (a.trial_stat)
+                            a.trial_stat[(int64_t)U.c * a.n_trials + kk] = valid ? v : __int_as_float(0x7fc00000);
+                        if (valid) key = make_key(v, (uint32_t)kk);
                     } else {
                         const double fpk = a.f_min + (double)U.peak_mult * a.coarse_df;
                         const double fr = fpk + (double)kk * a.step;
@@ -509,12 +517,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
             if (U.empty) continue;
             const int64_t off = a.cp[U.c].off;
             const bool tab = U.n <= kTcTablePoints;
+            const uint64_t mf = tc_mult(a, U, f);         // this producer's frequency multiplier
             if (tab) {
                 // every producer is done with the previous unit's table
                 asm volatile("bar.sync 2, 256;" ::: "memory");
                 for (int j = pt; ok && j < U.n; j += kTcProducers) {
                     const uint64_t stp = a.ph_step[off + j];
-                    uint64_t ph0 = a.ph_base[off + j] + (uint64_t)U.kfirst * stp;
+                    uint64_t ph0 = a.ph_base[off + j] + tc_base_mult(a, U) * stp;
                     if (a.stage == kStageFine) ph0 += U.peak_mult * a.ph_coarse[off + j];
                     sPh[j] = make_ulonglong2(ph0, stp);
                 }
@@ -532,9 +541,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                         if (j0 + p < U.n) {
                             if (tab) {
                                 const ulonglong2 e = sPh[j0 + p];
-                                v = (uint32_t)((e.x + (uint64_t)f * e.y) >> 32);
+                                v = (uint32_t)((e.x + mf * e.y) >> 32);
                             } else {
-                                v = tc_phase_u32(a, U, off, j0 + p, f);
+                                v = tc_phase_u32(a, U, off, j0 + p, mf);
                             }
                         }
                         pu[p] = v;

@@ -4,6 +4,8 @@ host-side Bessel coefficients match the paper's series (Eq. (taylor))."""
 import ctypes
 import os
 import re
+import subprocess
+import tempfile
 
 import numpy as np
 import pytest
@@ -28,9 +30,30 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, name), name
 
 
-def test_struct_sizes_match_header_layout():
-    assert ctypes.sizeof(cp.cp_freq_grid) == 56
-    assert ctypes.sizeof(cp.cp_options) == 48
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a header struct, from a C program compiled against include/cp.h."""
+    body = 'printf("%%zu", sizeof(%s));' % struct
+    for f in fields:
+        body += 'printf(" %%zu", offsetof(%s, %s));' % (struct, f)
+    src = '#include <stdio.h>\n#include <stddef.h>\n#include "cp.h"\nint main(void){%s return 0;}\n' % body
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        return [int(x) for x in subprocess.check_output([exe]).split()]
+
+
+@pytest.mark.parametrize("cls,name", [(cp.cp_freq_grid, "cp_freq_grid"), (cp.cp_options, "cp_options"),
+                                      (cp.cp_plan_info, "cp_plan_info")])
+def test_binding_structs_match_header_layout(cls, name):
+    fields = [f for f, _ in cls._fields_]
+    got = _c_layout(name, fields)
+    want = [ctypes.sizeof(cls)] + [getattr(cls, f).offset for f in fields]
+    assert got == want
+
+
+def test_default_options():
     o = cp.cp_default_options()
     assert o.sigma_t == pytest.approx(0.3) and o.alpha == 1.0 and o.use_graph == 1
     assert o.form == cp.CP_FORM_DIRECT and o.input_memory == cp.CP_MEM_HOST
@@ -77,6 +100,15 @@ def test_argument_validation_precedes_device_use():
     assert _plan_status([0, 5], sigma_t=0.0) == cp.CP_EINVAL
     assert _plan_status([0, 5], alpha=-1.0) == cp.CP_EINVAL
     assert _plan_status([0, 5], sigma_t_mode=7) == cp.CP_EINVAL
+    bands = dict(bands=True, n_bands=3, trials_per_band=150)
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 10, **dict(bands, n_bands=0))) == cp.CP_EINVAL
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 10, **dict(bands, n_bands=11))) == cp.CP_EINVAL
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 10, **dict(bands, trials_per_band=0))) == cp.CP_EINVAL
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 10, **dict(bands, trials_per_band=513))) == cp.CP_EINVAL
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 1e-5, 50001, **bands)) == cp.CP_EUNSUPPORTED
+    g = cp.make_grid(0.01, 0.01, 10)
+    g.hierarchical = 3
+    assert _plan_status([0, 5], grid=g) == cp.CP_EINVAL
 
 
 def test_no_device_is_an_error_not_a_fallback():
