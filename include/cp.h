@@ -80,7 +80,7 @@ enum { CP_MEM_HOST = 0, CP_MEM_DEVICE = 1 };
  *   3. D_b = sum of |d_i| over the d_i whose sample i is in band b (FP64);
  *   4. the n_bands bands of largest D (equal D: lower band first);
  *   5. for each, the spectral window S_b(f) = |sum_{i in b} exp(i 2 pi f t_i)|^2
- *      of Eq. (bands) on the uniform grid above (n_freq <= CP_BANDS_MAX_FREQ);
+ *      of Eq. (bands) on the uniform grid above;
  *   6. the trials_per_band highest local maxima of S_b (local maximum and
  *      tie rule as above), leaving out the one-day frequencies
  *      |1/f - 1| < 1e-4 (FP64).
@@ -90,7 +90,6 @@ enum { CP_MEM_HOST = 0, CP_MEM_DEVICE = 1 };
  * index k.  cp_trial_frequencies returns the list and its nCKP values.
  */
 enum { CP_SEARCH_FULL = 0, CP_SEARCH_COARSE_FINE = 1, CP_SEARCH_BANDS = 2 };
-#define CP_BANDS_MAX_FREQ 50000
 #define CP_BANDS_MAX_TRIALS 512
 
 typedef struct {

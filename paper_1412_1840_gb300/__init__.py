@@ -28,7 +28,7 @@ CP_DTYPE_FP16, CP_DTYPE_BF16 = 0, 1
 CP_SIGMA_T_FIXED, CP_SIGMA_T_PER_CURVE, CP_SIGMA_T_RULE = 0, 1, 2
 CP_MEM_HOST, CP_MEM_DEVICE = 0, 1
 CP_SEARCH_FULL, CP_SEARCH_COARSE_FINE, CP_SEARCH_BANDS = 0, 1, 2
-CP_BANDS_MAX_FREQ, CP_BANDS_MAX_TRIALS = 50000, 512
+CP_BANDS_MAX_TRIALS = 512
 
 
 class CpError(RuntimeError):

@@ -725,9 +725,6 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             return fail(CP_EINVAL, "cp_plan: n_bands must be in [1, 10]");
         if (g.trials_per_band < 1 || g.trials_per_band > kBandsMaxTrials)
             return fail(CP_EINVAL, "cp_plan: trials_per_band must be in [1, " + std::to_string(kBandsMaxTrials) + "]");
-        if (g.n_freq > kBandsMaxFreq)
-            return fail(CP_EUNSUPPORTED, "cp_plan: the bands method holds each spectral window in shared memory; "
-                                         "n_freq must be <= " + std::to_string(kBandsMaxFreq));
         p->bands = true;
         p->n_trials = g.n_bands * g.trials_per_band;
         // grid indices of the one-day frequencies |1/f - 1| < 1e-4 (a contiguous range; the
@@ -1014,10 +1011,9 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     if (bnd) {
         int optin = 0;
         CP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-        if (window_smem_bytes((int)g.n_freq, p->max_band_points) + 4096 > (size_t)optin)
-            return fail(CP_EUNSUPPORTED, "cp_plan: spectral window of " + std::to_string(g.n_freq) +
-                                             " frequencies does not fit in shared memory");
-        CP_CUDA(prepare_bands_kernels(p->np2max, (int)g.n_freq, p->max_band_points));
+        if (window_smem_bytes(p->max_band_points, g.trials_per_band) + 4096 > (size_t)optin)
+            return fail(CP_EUNSUPPORTED, "cp_plan: spectral-window buffers do not fit in shared memory");
+        CP_CUDA(prepare_bands_kernels(p->np2max, p->max_band_points, g.trials_per_band));
     }
     for (int nm : {4, 8, 16, 32})
         if (p->class_count[class_rank(nm)]) CP_CUDA(prepare_tensor_kernel(nm));   // one CTA per SM

@@ -7,16 +7,18 @@
 //             the bands in descending order of D (equal D: lower band first)
 //   k_window  one CTA per (curve, kept band): the spectral window of
 //             Eq. (bands), S(f_k) = |sum_{i in band} exp(i 2 pi f_k t_i)|^2,
-//             on the uniform grid f_k = f_min + k df, held whole in shared
-//             memory; then the n_t highest local maxima (one-day frequencies
-//             left out) by a four-pass radix select on the value bits.
+//             on the uniform grid f_k = f_min + k df, one segment of the grid
+//             at a time in shared memory; each segment's n_t highest local
+//             maxima (one-day frequencies left out) by a four-pass radix
+//             select on the value bits, merged into a running sorted list.
 //
 // Phases: exp(i 2 pi f_k t_i) with t_i - t0 (the window is invariant to a
 // common time shift) from the exact 64-bit fixed-point phases
 // base_i = frac(f_min (t_i - t0)) and step_i = frac(df (t_i - t0)) of the
-// curve statistics pass: thread t evaluates k = k0 + t + 512 q (q < 16) by
-// one sincos at k0 + t and fifteen FP32 rotations by exp(i 2 pi 512 step_i),
-// whose angle is also taken exactly from 512 step_i mod 1.
+// curve statistics pass: thread t evaluates k = k0 + t + 256 q (q < 16) by
+// one sincos at k0 + t, one complex product for q = 8, and seven packed
+// f32x2 rotations by exp(i 2 pi 256 step_i); both rotation angles are taken
+// exactly from 256 step_i and 2048 step_i mod 1.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -25,8 +27,10 @@
 namespace cpk {
 
 constexpr int kBandsThreads = 256;
-constexpr int kWinThreads = 512;
+constexpr int kWinThreads = 256;
 constexpr int kWinRun = 16;                    // frequencies per thread per pass (stride kWinThreads)
+constexpr int kWinHalf = kWinRun / 2;          // q and q + kWinHalf share an f32x2 register
+constexpr int kWinSeg = 2 * kWinThreads * kWinRun - 2;   // grid points per segment (two passes with neighbours)
 
 // ===========================================================================
 // k_bands
@@ -122,42 +126,86 @@ __global__ void __launch_bounds__(kBandsThreads) k_bands(const BandsArgs a)
 }
 
 // ===========================================================================
-// k_window
+// k_window: one CTA per (curve, kept band).  The grid is walked in segments
+// of kWinSeg points; for each, S is computed (plus one neighbour on each
+// side for the local-maximum test), the segment's n_t highest admissible
+// maxima are selected and sorted, and merged into the running sorted list.
+// The n_t highest of the whole grid are among the union of the per-segment
+// n_t highest, so the result is exact.
 // ===========================================================================
+
+__host__ __device__ inline int pow2_at_least(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
 
 // Shared-memory layout of k_window (bytes from the dynamic base).
 struct WinLayout {
-    size_t s, mask, pts, rot, sel, total;
+    size_t s, mask, pts, rot, lists, total;
 };
 
-__host__ __device__ inline WinLayout win_layout(int n_freq, int max_band_points)
+__host__ __device__ inline WinLayout win_layout(int max_band_points, int n_t)
 {
     WinLayout L;
-    const size_t kpad = ((size_t)n_freq + 3) & ~(size_t)3;
-    const size_t words = (((size_t)n_freq + 31) / 32 + 3) & ~(size_t)3;
     L.s = 0;
-    L.mask = L.s + kpad * sizeof(float);
-    L.pts = L.mask + words * sizeof(uint32_t);
-    L.rot = L.pts + (size_t)max_band_points * 2 * sizeof(uint64_t);
-    L.sel = L.rot + (size_t)max_band_points * 2 * sizeof(float);
-    L.total = L.sel + (size_t)kBandsMaxTrials * sizeof(unsigned long long);
+    L.mask = L.s + (size_t)(kWinSeg + 2 + 2) * sizeof(float);
+    L.pts = L.mask + (size_t)((kWinSeg + 31) / 32 + 2) * sizeof(uint32_t);
+    L.pts = (L.pts + 15) & ~(size_t)15;
+    L.rot = L.pts + (size_t)max_band_points * sizeof(ulonglong2);
+    L.lists = L.rot + (size_t)max_band_points * sizeof(float4);
+    L.total = L.lists + 3 * (size_t)pow2_at_least(n_t) * sizeof(unsigned long long);
     return L;
 }
 
-__device__ __forceinline__ bool win_cand(const uint32_t* mask, int k)
+__device__ __forceinline__ bool win_cand(const uint32_t* mask, int j)
 {
-    return (mask[k >> 5] >> (k & 31)) & 1u;
+    return (mask[j >> 5] >> (j & 31)) & 1u;
 }
 
-__global__ void __launch_bounds__(kWinThreads, 1) k_window(const WindowArgs a)
+// Descending bitonic sort of n (a power of two) 64-bit keys in shared memory.
+__device__ __forceinline__ void sort_desc(unsigned long long* v, int n, int tid)
+{
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            __syncthreads();
+            for (int i = tid; i < n; i += kWinThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool down = (i & k) == 0;
+                    const unsigned long long u = v[i], w = v[ixj];
+                    if ((u < w) == down) { v[i] = w; v[ixj] = u; }
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Number of entries of the descending list v[0..n) greater than x.
+__device__ __forceinline__ int count_greater(const unsigned long long* v, int n, unsigned long long x)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (v[mid] > x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const WinLayout Lo = win_layout(a.n_freq, a.max_band_points);
+    const WinLayout Lo = win_layout(a.max_band_points, a.n_t);
     float* S = reinterpret_cast<float*>(smem + Lo.s);
     uint32_t* mask = reinterpret_cast<uint32_t*>(smem + Lo.mask);
     ulonglong2* pts = reinterpret_cast<ulonglong2*>(smem + Lo.pts);
-    float2* rot = reinterpret_cast<float2*>(smem + Lo.rot);
-    unsigned long long* sel = reinterpret_cast<unsigned long long*>(smem + Lo.sel);
+    float4* rot = reinterpret_cast<float4*>(smem + Lo.rot);
+    const int cap = pow2_at_least(a.n_t);
+    unsigned long long* sel = reinterpret_cast<unsigned long long*>(smem + Lo.lists);
+    unsigned long long* run0 = sel + cap;
+    unsigned long long* run1 = run0 + cap;
     __shared__ uint32_t hist[256];
     __shared__ int s_wsum[kWinThreads / 32];
     __shared__ int s_total, s_nsel, s_m;
@@ -172,7 +220,8 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_window(const WindowArgs a)
     const int n = a.cp[c].n;
     const int band = a.kept[(int64_t)c * a.n_bands + b];
 
-    // 1. the band's samples, in sample order: (base, step) phases and the rotation exp(i 2 pi 512 step)
+    // 1. the band's samples, in sample order: phases (base, step) and the rotations
+    //    exp(i 2 pi 256 step), exp(i 2 pi 2048 step)
     if (tid == 0) s_m = 0;
     __syncthreads();
     for (int i0 = 0; i0 < n; i0 += kWinThreads) {
@@ -187,9 +236,10 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_window(const WindowArgs a)
         if (in && pos < a.max_band_points) {   // a band never exceeds ceil(N/10) samples
             const uint64_t st = a.ph_step[off + i];
             pts[pos] = make_ulonglong2(a.ph_base[off + i], st);
-            float sr, cr;
+            float sr, cr, s8, c8;
             sincos2pi_turns((uint32_t)((st * (uint64_t)kWinThreads) >> 32), sr, cr);
-            rot[pos] = make_float2(cr, sr);
+            sincos2pi_turns((uint32_t)((st * (uint64_t)(kWinThreads * kWinHalf)) >> 32), s8, c8);
+            rot[pos] = make_float4(cr, sr, c8, s8);
         }
         __syncthreads();
         if (tid == 0) {
@@ -199,190 +249,229 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_window(const WindowArgs a)
         }
         __syncthreads();
     }
-    const int m = s_m;
+    const int m = min(s_m, a.max_band_points);
 
-    // 2. spectral window, Eq. (bands): thread tid covers k = k0 + tid + 512 q
-    for (int k0 = 0; k0 < K; k0 += kWinThreads * kWinRun) {
-        const int kb = k0 + tid;
-        float re[kWinRun], im[kWinRun];
-#pragma unroll
-        for (int q = 0; q < kWinRun; q++) { re[q] = 0.f; im[q] = 0.f; }
-        if (kb < K) {
-            for (int p = 0; p < m; p++) {
-                const ulonglong2 e = pts[p];
-                const float2 r = rot[p];
-                float zi, zr;
-                sincos2pi_turns((uint32_t)((e.x + (uint64_t)kb * e.y) >> 32), zi, zr);
-#pragma unroll
-                for (int q = 0; q < kWinRun; q++) {
-                    re[q] += zr;
-                    im[q] += zi;
-                    const float nr = fmaf(zr, r.x, -zi * r.y);
-                    const float ni = fmaf(zr, r.y, zi * r.x);
-                    zr = nr;
-                    zi = ni;
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kWinRun; q++) {
-            const int k = kb + q * kWinThreads;
-            // a one-sample band is exactly 1 (|exp(i x)|^2), not cos^2 + sin^2 with rounding noise
-            if (k < K) S[k] = m <= 1 ? (float)m : fmaf(re[q], re[q], im[q] * im[q]);
-        }
-    }
-    if (tid == 0) { s_total = 0; s_nsel = 0; }
-    __syncthreads();
+    unsigned long long* run = run0;   // running list: the n_t highest so far, descending
+    unsigned long long* nxt = run1;
+    int rc = 0;
+    for (int lo = 0; lo < K; lo += kWinSeg) {
+        const int hi = min(K, lo + kWinSeg);
+        const int v0 = max(lo - 1, 0), v1 = min(hi + 1, K);   // S[k - v0] holds k in [v0, v1)
+        const int nv = v1 - v0;
 
-    // 3. admissible local maxima: S[k] > S[k-1], S[k] >= S[k+1] (ends: one neighbour), not one-day
-    const int words = (K + 31) >> 5;
-    int local = 0;
-    for (int w = warp; w < words; w += NW) {
-        const int k = (w << 5) + lane;
-        bool ok = false;
-        if (k < K) {
-            const float v = S[k];
-            ok = (k == 0 || v > S[k - 1]) && (k == K - 1 || v >= S[k + 1]) && !(k >= a.ex_lo && k <= a.ex_hi);
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
-        if (lane == 0) {
-            mask[w] = bal;
-            local += __popc(bal);
-        }
-    }
-    if (lane == 0) atomicAdd(&s_total, local);
-    __syncthreads();
-    const int total = s_total;
-
-    // 4. threshold: the n_t-th largest value among the candidates (radix select on orderable bits)
-    uint32_t T = 0u;        // select keys > T, plus `need` of the keys == T (lowest k first)
-    int need = 0;
-    bool take_all_eq = true;
-    if (total > n_t) {
-        if (tid == 0) { s_prefix = 0u; s_need = n_t; }
-        for (int pass = 0; pass < 4; pass++) {
-            const int shift = 24 - 8 * pass;
-            for (int i = tid; i < 256; i += kWinThreads) hist[i] = 0u;
-            __syncthreads();
-            const uint32_t prefix = s_prefix;
-            for (int k = tid; k < K; k += kWinThreads) {
-                if (!win_cand(mask, k)) continue;
-                const uint32_t key = orderable(S[k]);
-                if (pass == 0 || (key >> (shift + 8)) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
-            }
-            __syncthreads();
-            if (warp == 0) {
-                // lane l owns digits 255-8l-7 .. 255-8l; find the digit holding the need-th largest
-                const int nd = s_need;
-                uint32_t h[8];
-                uint32_t sum = 0;
+        // 2. spectral window, Eq. (bands): thread tid covers k = v0 + p0 + tid + 256 q, q < 16, with
+        //    q and q + 8 in the two lanes of an f32x2 register, rotated by exp(i 2 pi 256 step)
+        for (int p0 = 0; p0 < nv; p0 += kWinThreads * kWinRun) {
+            const int j0 = p0 + tid;
+            f2 re2[kWinHalf], im2[kWinHalf];
 #pragma unroll
-                for (int x = 0; x < 8; x++) {
-                    h[x] = hist[255 - 8 * lane - x];
-                    sum += h[x];
-                }
-                uint32_t incl = sum;
+            for (int q = 0; q < kWinHalf; q++) { re2[q] = 0ull; im2[q] = 0ull; }
+            if (j0 < nv) {
+                const uint64_t kb = (uint64_t)(v0 + j0);
+                ulonglong2 en = pts[0];
+                float4 rn = rot[0];
+                for (int p = 0; p < m; p++) {
+                    const ulonglong2 e = en;       // this point; the next one's loads are in flight
+                    const float4 r = rn;
+                    const int pn = p + 1 < m ? p + 1 : p;
+                    en = pts[pn];
+                    rn = rot[pn];
+                    float zi, zr;
+                    sincos2pi_turns((uint32_t)((e.x + kb * e.y) >> 32), zi, zr);
+                    const float zr8 = fmaf(zr, r.z, -zi * r.w), zi8 = fmaf(zr, r.w, zi * r.z);
+                    f2 ZR = pk(zr, zr8), ZI = pk(zi, zi8);
+                    const f2 CR = pk(r.x, r.x), SR = pk(r.y, r.y), NSR = pk(-r.y, -r.y);
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const uint32_t excl = incl - sum;
-                if (excl < (uint32_t)nd && (uint32_t)nd <= incl) {
-                    uint32_t cum = excl;
-#pragma unroll
-                    for (int x = 0; x < 8; x++) {
-                        if (cum + h[x] >= (uint32_t)nd) {
-                            const uint32_t d = 255u - 8u * lane - x;
-                            s_prefix = (prefix << 8) | d;
-                            s_need = nd - (int)cum;
-                            s_eq = (int)h[x];
-                            break;
-                        }
-                        cum += h[x];
+                    for (int q = 0; q < kWinHalf; q++) {
+                        re2[q] = add2(re2[q], ZR);
+                        im2[q] = add2(im2[q], ZI);
+                        const f2 nr = fma2(ZR, CR, mul2(ZI, NSR));
+                        const f2 ni = fma2(ZR, SR, mul2(ZI, CR));
+                        ZR = nr;
+                        ZI = ni;
                     }
                 }
             }
-            __syncthreads();
-        }
-        T = s_prefix;
-        need = s_need;
-        take_all_eq = s_eq == need;
-    }
-
-    // 5. collect: keys > T (and == T when all of them are taken), unordered
-    for (int k = tid; k < K; k += kWinThreads) {
-        if (!win_cand(mask, k)) continue;
-        const uint32_t key = orderable(S[k]);
-        if (key > T || (key == T && take_all_eq && total > n_t)) {
-            const int pos = atomicAdd(&s_nsel, 1);
-            if (pos < kBandsMaxTrials) sel[pos] = ((unsigned long long)key << 32) | (0xffffffffu - (uint32_t)k);
-        }
-    }
-    __syncthreads();
-    if (!take_all_eq) {
-        // ties at the threshold: the `need` lowest k, by an ordered scan
-        int taken = 0;
-        for (int k0 = 0; k0 < K && taken < need; k0 += kWinThreads) {
-            const int k = k0 + tid;
-            const bool eq = k < K && win_cand(mask, k) && orderable(S[k]) == T;
-            const uint32_t bal = __ballot_sync(0xffffffffu, eq);
-            if (lane == 0) s_wsum[warp] = __popc(bal);
-            __syncthreads();
-            int before = taken, chunk = 0;
-            for (int w = 0; w < NW; w++) {
-                if (w < warp) before += s_wsum[w];
-                chunk += s_wsum[w];
+#pragma unroll
+            for (int q = 0; q < kWinHalf; q++) {
+                float rl, rh, il, ih;
+                upk(re2[q], rl, rh);
+                upk(im2[q], il, ih);
+                const int ja = j0 + q * kWinThreads, jb = ja + kWinHalf * kWinThreads;
+                // a one-sample band is exactly 1 (|exp(i x)|^2), not cos^2 + sin^2 with rounding noise
+                if (ja < nv) S[ja] = m <= 1 ? (float)m : fmaf(rl, rl, il * il);
+                if (jb < nv) S[jb] = m <= 1 ? (float)m : fmaf(rh, rh, ih * ih);
             }
-            if (eq) {
-                const int rank = before + __popc(bal & ((1u << lane) - 1u));
-                if (rank < need) {
+        }
+        if (tid == 0) { s_total = 0; s_nsel = 0; }
+        __syncthreads();
+
+        // 3. admissible local maxima of the segment: S[k] > S[k-1], S[k] >= S[k+1]
+        //    (grid ends: one neighbour), one-day frequencies left out; once the running
+        //    list is full, only keys above its last entry can still enter it
+        const unsigned long long floor_key = rc == n_t ? run[n_t - 1] : 0ull;
+        const int len = hi - lo;
+        const int words = (len + 31) >> 5;
+        int local = 0;
+        for (int w = warp; w < words; w += NW) {
+            const int j = (w << 5) + lane;      // segment position, k = lo + j
+            const int k = lo + j;
+            bool ok = false;
+            if (j < len) {
+                const int x = k - v0;
+                const float v = S[x];
+                ok = (k == 0 || v > S[x - 1]) && (k == K - 1 || v >= S[x + 1]) && !(k >= a.ex_lo && k <= a.ex_hi) &&
+                     (((unsigned long long)orderable(v) << 32) | (0xffffffffu - (uint32_t)k)) > floor_key;
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) {
+                mask[w] = bal;
+                local += __popc(bal);
+            }
+        }
+        if (lane == 0 && local) atomicAdd(&s_total, local);
+        __syncthreads();
+        const int total = s_total;
+
+        // 4. the segment's threshold: its n_t-th largest candidate value (radix select on the
+        //    orderable bits, warp-aggregated histogram updates)
+        uint32_t T = 0u;        // take keys > T, plus `need` keys == T (lowest k first)
+        int need = 0;
+        bool take_all_eq = true;
+        if (total > n_t) {
+            if (tid == 0) { s_prefix = 0u; s_need = n_t; }
+            for (int pass = 0; pass < 4; pass++) {
+                const int shift = 24 - 8 * pass;
+                for (int i = tid; i < 256; i += kWinThreads) hist[i] = 0u;
+                __syncthreads();
+                const uint32_t prefix = s_prefix;
+                for (int j0 = 0; j0 < len; j0 += kWinThreads) {
+                    const int j = j0 + tid;
+                    bool take = false;
+                    uint32_t d = 0u;
+                    if (j < len && win_cand(mask, j)) {
+                        const uint32_t key = orderable(S[lo + j - v0]);
+                        take = pass == 0 || (key >> (shift + 8)) == prefix;
+                        d = (key >> shift) & 255u;
+                    }
+                    const uint32_t peers = __match_any_sync(0xffffffffu, take ? d : 256u + (uint32_t)lane);
+                    if (take && lane == __ffs(peers) - 1) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    // lane l owns digits 255-8l .. 248-8l; find the digit holding the need-th largest
+                    const int nd = s_need;
+                    uint32_t h[8];
+                    uint32_t sum = 0;
+#pragma unroll
+                    for (int x = 0; x < 8; x++) {
+                        h[x] = hist[255 - 8 * lane - x];
+                        sum += h[x];
+                    }
+                    uint32_t incl = sum;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const uint32_t excl = incl - sum;
+                    if (excl < (uint32_t)nd && (uint32_t)nd <= incl) {
+                        uint32_t cum = excl;
+#pragma unroll
+                        for (int x = 0; x < 8; x++) {
+                            if (cum + h[x] >= (uint32_t)nd) {
+                                s_prefix = (prefix << 8) | (255u - 8u * lane - x);
+                                s_need = nd - (int)cum;
+                                s_eq = (int)h[x];
+                                break;
+                            }
+                            cum += h[x];
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            T = s_prefix;
+            need = s_need;
+            take_all_eq = s_eq == need;
+        }
+
+        // 5. collect: keys > T (and == T when all of them are taken), unordered
+        for (int j0 = 0; j0 < len; j0 += kWinThreads) {
+            const int j = j0 + tid;
+            if (j < len && win_cand(mask, j)) {
+                const uint32_t key = orderable(S[lo + j - v0]);
+                if (key > T || (key == T && take_all_eq && total > n_t)) {
                     const int pos = atomicAdd(&s_nsel, 1);
-                    if (pos < kBandsMaxTrials) sel[pos] = ((unsigned long long)T << 32) | (0xffffffffu - (uint32_t)k);
+                    if (pos < n_t) sel[pos] = ((unsigned long long)key << 32) | (0xffffffffu - (uint32_t)(lo + j));
                 }
             }
-            taken += chunk;
-            __syncthreads();
         }
-    }
-    __syncthreads();
-    const int nsel = min(s_nsel, n_t);
+        __syncthreads();
+        if (!take_all_eq) {
+            // ties at the threshold: the `need` lowest k, by an ordered scan
+            int taken = 0;
+            for (int j0 = 0; j0 < len && taken < need; j0 += kWinThreads) {
+                const int j = j0 + tid;
+                const bool eq = j < len && win_cand(mask, j) && orderable(S[lo + j - v0]) == T;
+                const uint32_t bal = __ballot_sync(0xffffffffu, eq);
+                if (lane == 0) s_wsum[warp] = __popc(bal);
+                __syncthreads();
+                int before = taken, chunk = 0;
+                for (int w = 0; w < NW; w++) {
+                    if (w < warp) before += s_wsum[w];
+                    chunk += s_wsum[w];
+                }
+                if (eq) {
+                    const int r = before + __popc(bal & ((1u << lane) - 1u));
+                    if (r < need) {
+                        const int pos = atomicAdd(&s_nsel, 1);
+                        if (pos < n_t) sel[pos] = ((unsigned long long)T << 32) | (0xffffffffu - (uint32_t)(lo + j));
+                    }
+                }
+                taken += chunk;
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        const int nsel = min(s_nsel, n_t);
+        const int np2 = pow2_at_least(nsel);
+        for (int i = nsel + tid; i < np2; i += kWinThreads) sel[i] = 0ull;
+        sort_desc(sel, np2, tid);
 
-    // 6. order: value descending, ties to the lower k (bitonic sort of the keys, descending)
-    int np2 = 1;
-    while (np2 < nsel) np2 <<= 1;
-    for (int i = nsel + tid; i < np2; i += kWinThreads) sel[i] = 0ull;
-    for (int k = 2; k <= np2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            __syncthreads();
-            for (int i = tid; i < np2; i += kWinThreads) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const bool down = (i & k) == 0;
-                    const unsigned long long u = sel[i], v = sel[ixj];
-                    if ((u < v) == down) { sel[i] = v; sel[ixj] = u; }
-                }
-            }
+        // 6. merge the sorted segment list into the running list (keys are unique: rank by counting)
+        for (int i = tid; i < rc; i += kWinThreads) {
+            const int r = i + count_greater(sel, nsel, run[i]);
+            if (r < n_t) nxt[r] = run[i];
         }
+        for (int i = tid; i < nsel; i += kWinThreads) {
+            const int r = i + count_greater(run, rc, sel[i]);
+            if (r < n_t) nxt[r] = sel[i];
+        }
+        rc = min(rc + nsel, n_t);
+        unsigned long long* t = run;
+        run = nxt;
+        nxt = t;
+        __syncthreads();
     }
-    __syncthreads();
+
     int32_t* out = a.trials + ((int64_t)c * a.n_bands + b) * n_t;
     for (int r = tid; r < n_t; r += kWinThreads)
-        out[r] = r < nsel ? (int32_t)(0xffffffffu - (uint32_t)(sel[r] & 0xffffffffu)) : -1;
+        out[r] = r < rc ? (int32_t)(0xffffffffu - (uint32_t)(run[r] & 0xffffffffu)) : -1;
 }
 
 // ---------------------------------------------------------------------------
 size_t bands_smem_bytes(int np2max) { return (size_t)np2max * (sizeof(unsigned long long) + 1); }
 
-size_t window_smem_bytes(int n_freq, int max_band_points) { return win_layout(n_freq, max_band_points).total; }
+size_t window_smem_bytes(int max_band_points, int n_t) { return win_layout(max_band_points, n_t).total; }
 
-cudaError_t prepare_bands_kernels(int np2max, int n_freq, int max_band_points)
+cudaError_t prepare_bands_kernels(int np2max, int max_band_points, int n_t)
 {
     cudaError_t e = cudaFuncSetAttribute(k_bands, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bands_smem_bytes(np2max));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)window_smem_bytes(n_freq, max_band_points));
+                                (int)window_smem_bytes(max_band_points, n_t));
 }
 
 cudaError_t launch_bands(const BandsArgs& a, int n_curves, cudaStream_t s)
@@ -395,7 +484,7 @@ cudaError_t launch_window(const WindowArgs& a, cudaStream_t s)
 {
     const int64_t ctas = (int64_t)a.n_curves * a.n_bands;
     if (ctas <= 0) return cudaSuccess;
-    k_window<<<(unsigned)ctas, kWinThreads, window_smem_bytes(a.n_freq, a.max_band_points), s>>>(a);
+    k_window<<<(unsigned)ctas, kWinThreads, window_smem_bytes(a.max_band_points, a.n_t), s>>>(a);
     return cudaGetLastError();
 }
 

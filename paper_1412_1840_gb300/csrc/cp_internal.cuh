@@ -201,7 +201,6 @@ struct TensorArgs {
 };
 
 // Bands method, Section 3.1 (cp_bands.cu).
-constexpr int kBandsMaxFreq = CP_BANDS_MAX_FREQ;
 constexpr int kBandsMaxTrials = CP_BANDS_MAX_TRIALS;
 
 struct BandsArgs {
@@ -228,8 +227,8 @@ struct WindowArgs {
 };
 
 size_t bands_smem_bytes(int np2max);
-size_t window_smem_bytes(int n_freq, int max_band_points);
-cudaError_t prepare_bands_kernels(int np2max, int n_freq, int max_band_points);
+size_t window_smem_bytes(int max_band_points, int n_t);
+cudaError_t prepare_bands_kernels(int np2max, int max_band_points, int n_t);
 cudaError_t launch_bands(const BandsArgs& a, int n_curves, cudaStream_t s);
 cudaError_t launch_window(const WindowArgs& a, cudaStream_t s);
 
@@ -322,6 +321,16 @@ __device__ __forceinline__ void sincos2pi_turns(uint32_t U, float& s, float& c)
     case 2: s = -sx; c = -cx; break;
     default: s = -cx; c = sx; break;
     }
+}
+
+// sin(2 pi x), cos(2 pi x) for x = U / 2^32 from the SFU approximations on
+// the exactly reduced angle in [-pi, pi): absolute error below 1e-6, for
+// operands that are rounded to 16-bit floats afterwards.
+__device__ __forceinline__ void sincos2pi_turns_sfu(uint32_t U, float& s, float& c)
+{
+    const float x = (float)(int32_t)U * 1.4629180792671596e-09f;   // 2 pi / 2^32
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
 }
 
 __device__ __forceinline__ float ex2_approx(float x)

@@ -37,6 +37,11 @@ constexpr int kTcStageBytes = 2 * kTcA + kTcB;   // W' tiles of two M-tiles + on
 constexpr int kTcCols = 256;           // columns per unit
 constexpr int kTcProducers = 256;      // warps 6..13
 constexpr int kTcTablePoints = 1024;   // per-unit phase table in shared memory (producers)
+// Table slot of point j: one 16-byte pad after every 8 entries, so that the
+// eight j-octets a warp reads at once (128 bytes apart unpadded) fall on
+// different banks.
+__device__ __forceinline__ int tc_tab(int j) { return j + (j >> 3); }
+constexpr int kTcTableSlots = kTcTablePoints + kTcTablePoints / 8;
 
 __host__ __device__ inline int tc_mtiles(int n) { return (n + 127) / 128; }
 __host__ __device__ inline int tc_kchunks(int n) { return (n + 63) / 64; }
@@ -232,30 +237,35 @@ __device__ __forceinline__ TcUnit tc_decode(const TensorArgs& a, int64_t u)
 // table base: f for the uniform stages (base = ph_base + kfirst * step), the
 // grid index of list position kfirst + f for the list stage (base = ph_base;
 // a missing entry evaluates k = 0 and is never emitted).
+template <bool LIST>
 __device__ __forceinline__ uint64_t tc_mult(const TensorArgs& a, const TcUnit& U, int f)
 {
-    if (a.stage != kStageList) return (uint64_t)f;
+    if (!LIST) return (uint64_t)f;
     const int64_t q = U.kfirst + f;
     return q < a.n_trials ? (uint64_t)max(a.trials[(int64_t)U.c * a.n_trials + q], 0) : 0ull;
 }
 
+template <bool LIST>
 __device__ __forceinline__ uint64_t tc_base_mult(const TensorArgs& a, const TcUnit& U)
 {
-    return a.stage == kStageList ? 0ull : (uint64_t)U.kfirst;
+    return LIST ? 0ull : (uint64_t)U.kfirst;
 }
 
+template <bool LIST>
 __device__ __forceinline__ uint32_t tc_phase_u32(const TensorArgs& a, const TcUnit& U, int64_t off, int i,
                                                  uint64_t mult)
 {
     const uint64_t st = a.ph_step[off + i];
-    uint64_t ph = a.ph_base[off + i] + (tc_base_mult(a, U) + mult) * st;
+    uint64_t ph = a.ph_base[off + i] + (tc_base_mult<LIST>(a, U) + mult) * st;
     if (a.stage == kStageFine) ph += U.peak_mult * a.ph_coarse[off + i];
     return (uint32_t)(ph >> 32);
 }
 
 // Stages hold the W' tiles of two M-tiles and one Z tile: M-tiles 2P and
 // 2P+1 share every Z stage of their common K range (two TMEM accumulators).
-template <int NMAX, bool BF>
+// LIST: the list stage (explicit grid indices per curve); a separate
+// instantiation so that the uniform stages keep their rotation shortcut.
+template <int NMAX, bool BF, bool LIST>
 __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -382,7 +392,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
         const int lg = warp & 3;                      // TMEM lane group this warp may access
         const int row = lg * 32 + lane;
         const int ew = warp - 2;                      // epilogue warp index 0..3
-        const bool list = a.stage == kStageList;      // explicit frequencies: no rotation shortcut
+        constexpr bool list = LIST;                   // explicit frequencies: no rotation shortcut
         uint32_t m = 0;
         bool ok = true;
         for (int64_t u = a.unit_begin + blockIdx.x / a.ctas_per_unit; ok && u < a.unit_end; u += gridDim.x) {
@@ -403,7 +413,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                     live[h] = i < U.n;
                     if (live[h]) {
                         pstep[h] = a.ph_step[off + i];
-                        ph0[h] = a.ph_base[off + i] + tc_base_mult(a, U) * pstep[h];
+                        ph0[h] = a.ph_base[off + i] + tc_base_mult<LIST>(a, U) * pstep[h];
                         if (a.stage == kStageFine) ph0[h] += U.peak_mult * a.ph_coarse[off + i];
                     }
                 }
@@ -414,6 +424,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                 tc_fence_after();
 #pragma unroll 1
                 for (int h = 0; h < 2; h++) {
+                    // scalars, not the arrays indexed by h: this loop is not unrolled, and
+                    // indexing the arrays with h would place them in local memory
+                    const bool live_h = h ? live[1] : live[0];
+                    const uint64_t ph0_h = h ? ph0[1] : ph0[0];
+                    const uint64_t pstep_h = h ? pstep[1] : pstep[0];
                     const bool has = 2 * P + h < U.nmt;
                     float accf[FT];
                     if (has) {
@@ -421,12 +436,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                         float v[32];
                         // the angle of odd frequencies is the even one's rotated by one frequency step
                         float sr = 0.f, cr = 1.f, s1 = 0.f, c1 = 0.f;
-                        if (live[h]) sincos2pi_turns((uint32_t)(pstep[h] >> 32), sr, cr);
+                        if (live_h) sincos2pi_turns((uint32_t)(pstep_h >> 32), sr, cr);
 #pragma unroll
                         for (int f = 0; f < FT; f++) {
-                            if (live[h]) {
+                            if (live_h) {
                                 if ((f & 1) == 0 || list) {
-                                    sincos2pi_turns((uint32_t)((ph0[h] + tc_mult(a, U, f) * pstep[h]) >> 32), s1, c1);
+                                    sincos2pi_turns((uint32_t)((ph0_h + tc_mult<LIST>(a, U, f) * pstep_h) >> 32), s1, c1);
                                 } else {
                                     const float cn = fmaf(c1, cr, -s1 * sr), sn = fmaf(s1, cr, c1 * sr);
                                     c1 = cn;
@@ -444,7 +459,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                                 cp2 = cp1; sp2 = sp1;
                                 cp1 = cn; sp1 = sn;
                             }
-                            accf[f] = live[h] ? acc : 0.f;
+                            accf[f] = live_h ? acc : 0.f;
                         }
                     }
                     // release this accumulator (always, so the phases of both buffers advance per pair)
@@ -517,15 +532,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
             if (U.empty) continue;
             const int64_t off = a.cp[U.c].off;
             const bool tab = U.n <= kTcTablePoints;
-            const uint64_t mf = tc_mult(a, U, f);         // this producer's frequency multiplier
+            const uint64_t mf = tc_mult<LIST>(a, U, f);   // this producer's frequency multiplier
             if (tab) {
                 // every producer is done with the previous unit's table
                 asm volatile("bar.sync 2, 256;" ::: "memory");
                 for (int j = pt; ok && j < U.n; j += kTcProducers) {
                     const uint64_t stp = a.ph_step[off + j];
-                    uint64_t ph0 = a.ph_base[off + j] + tc_base_mult(a, U) * stp;
+                    uint64_t ph0 = a.ph_base[off + j] + tc_base_mult<LIST>(a, U) * stp;
                     if (a.stage == kStageFine) ph0 += U.peak_mult * a.ph_coarse[off + j];
-                    sPh[j] = make_ulonglong2(ph0, stp);
+                    sPh[tc_tab(j)] = make_ulonglong2(ph0, stp);
                 }
                 asm volatile("bar.sync 2, 256;" ::: "memory");
             }
@@ -540,10 +555,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                         uint32_t v = 0u;
                         if (j0 + p < U.n) {
                             if (tab) {
-                                const ulonglong2 e = sPh[j0 + p];
+                                const ulonglong2 e = sPh[tc_tab(j0 + p)];
                                 v = (uint32_t)((e.x + mf * e.y) >> 32);
                             } else {
-                                v = tc_phase_u32(a, U, off, j0 + p, mf);
+                                v = tc_phase_u32<LIST>(a, U, off, j0 + p, mf);
                             }
                         }
                         pu[p] = v;
@@ -553,7 +568,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
 #pragma unroll
                     for (int p = 0; p < 8; p++) {
                         float sv = 0.f, cv = 0.f;
-                        if (j0 + p < U.n) sincos2pi_turns(pu[p], sv, cv);
+                        if (j0 + p < U.n) sincos2pi_turns_sfu(pu[p], sv, cv);   // Z is rounded to 16 bits
                         c1[p] = cv;
                         cc[p] = cv; ss[p] = sv;           // n = 1
                         cm[p] = 1.f; sm[p] = 0.f;         // n = 0
@@ -594,14 +609,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
 }
 
 // ---------------------------------------------------------------------------
-size_t tensor_smem_bytes() { return (size_t)kTcStages * kTcStageBytes + kTcTablePoints * 16 + 1024; }
+size_t tensor_smem_bytes() { return (size_t)kTcStages * kTcStageBytes + kTcTableSlots * 16 + 1024; }
 
 int tensor_tiles_of(int n) { return tc_tiles_of(n); }
 
 template <int NMAX, bool BF>
 static cudaError_t set_tensor_smem()
 {
-    return cudaFuncSetAttribute(k_pair_tensor<NMAX, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_pair_tensor<NMAX, BF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tensor_smem_bytes());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_pair_tensor<NMAX, BF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tensor_smem_bytes());
 }
 
@@ -634,11 +652,16 @@ cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max,
 cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s)
 {
     const size_t b = tensor_smem_bytes();
-    const bool bf = a.bf16 != 0;
-#define CP_TC_LAUNCH(NM)                                                        \
-    case NM:                                                                    \
-        if (bf) k_pair_tensor<NM, true><<<grid, kTcThreads, b, s>>>(a);         \
-        else k_pair_tensor<NM, false><<<grid, kTcThreads, b, s>>>(a);           \
+    const bool bf = a.bf16 != 0, list = a.stage == kStageList;
+#define CP_TC_LAUNCH(NM)                                                                        \
+    case NM:                                                                                    \
+        if (list) {                                                                             \
+            if (bf) k_pair_tensor<NM, true, true><<<grid, kTcThreads, b, s>>>(a);               \
+            else k_pair_tensor<NM, false, true><<<grid, kTcThreads, b, s>>>(a);                 \
+        } else {                                                                                \
+            if (bf) k_pair_tensor<NM, true, false><<<grid, kTcThreads, b, s>>>(a);              \
+            else k_pair_tensor<NM, false, false><<<grid, kTcThreads, b, s>>>(a);                \
+        }                                                                                       \
         break;
     switch (a.n_max) {
         CP_TC_LAUNCH(4)
