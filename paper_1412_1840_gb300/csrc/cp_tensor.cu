@@ -30,12 +30,18 @@ namespace cpk {
 using namespace tc;
 
 constexpr int kTcStages = 3;
-constexpr int kTcThreads = 448;
 constexpr int kTcA = 16384;            // 128 x 64 x 2 B
 constexpr int kTcB = 32768;            // 256 x 64 x 2 B
 constexpr int kTcStageBytes = 2 * kTcA + kTcB;   // W' tiles of two M-tiles + one Z tile
 constexpr int kTcCols = 256;           // columns per unit
-constexpr int kTcProducers = 256;      // warps 6..13
+constexpr int kTcProducers = 256;      // the last 8 warps
+// Epilogue warps: 8 for up to 16 harmonics (two warps per TMEM lane group,
+// each taking half of the unit's frequencies), else 4; the drain of an
+// accumulator is on the MMA's critical path.  With 18 warps a quarter-SM
+// holds up to 5 of them, which caps registers at 96 per thread: enough
+// below 32 harmonics.
+__host__ __device__ constexpr int tc_ew(int nmax) { return nmax <= 16 ? 8 : 4; }
+__host__ __device__ constexpr int tc_threads(int nmax) { return 64 + 32 * tc_ew(nmax) + kTcProducers; }
 constexpr int kTcTablePoints = 1024;   // per-unit phase table in shared memory (producers)
 // Table slot of point j: one 16-byte pad after every 8 entries, so that the
 // eight j-octets a warp reads at once (128 bytes apart unpadded) fall on
@@ -266,7 +272,7 @@ __device__ __forceinline__ uint32_t tc_phase_u32(const TensorArgs& a, const TcUn
 // LIST: the list stage (explicit grid indices per curve); a separate
 // instantiation so that the uniform stages keep their rotation shortcut.
 template <int NMAX, bool BF, bool LIST>
-__global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs a)
+__global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const TensorArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -276,10 +282,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
     __shared__ uint64_t bar_tfull, bar_tempty[2], bar_drain;
     __shared__ uint32_t s_taddr;
     __shared__ int s_abort;
-    __shared__ float s_red[4][32];
+    __shared__ float s_red[8][32];
     __shared__ float s_acc[32];
 
     constexpr int FT = 128 / NMAX;                    // frequencies per unit (256 columns)
+    constexpr int EW = tc_ew(NMAX);                   // epilogue warps
+    constexpr int FH = FT / (EW / 4);                 // frequencies per epilogue warp
     constexpr int items = 8 * FT;                     // (j-octet, frequency) per stage
     // Stages produced concurrently.  A group owns every use of its stages, so
     // it never waits more than one barrier phase ahead; hence groups <= stages.
@@ -293,8 +301,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
             mbar_init(&bar_empty[s], 1);
         }
         mbar_init(&bar_tfull, 1);
-        mbar_init(&bar_tempty[0], 128);
-        mbar_init(&bar_tempty[1], 128);
+        mbar_init(&bar_tempty[0], 32 * EW);
+        mbar_init(&bar_tempty[1], 32 * EW);
         mbar_init(&bar_drain, 1);
         s_abort = 0;
         fence_mbar_init();
@@ -387,11 +395,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
             mbar_wait(&bar_drain, 0, &s_abort, 1u << 22);
             if (!ok) atomicOr(a.status, 2);
         }
-    } else if (warp < 6) {
-        // ---------------- epilogue: 128 threads, one TMEM lane (W' row) each ----------------
+    } else if (warp < 2 + EW) {
+        // ---------------- epilogue: one TMEM lane (W' row) per thread ----------------
         const int lg = warp & 3;                      // TMEM lane group this warp may access
         const int row = lg * 32 + lane;
-        const int ew = warp - 2;                      // epilogue warp index 0..3
+        const int ew = warp - 2;                      // epilogue warp index 0..EW-1
+        const int fh = ew >> 2;                       // which FH frequencies of the unit
+        const uint32_t hcol = (uint32_t)(fh * FH * 2 * NMAX);   // their first column (a multiple of 32)
         constexpr bool list = LIST;                   // explicit frequencies: no rotation shortcut
         uint32_t m = 0;
         bool ok = true;
@@ -419,7 +429,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                 }
                 mbar_wait(&bar_tfull, m & 1, &s_abort, a.wait_limit);
                 // agree on the outcome: every epilogue thread sees the abort flag after the barrier
-                asm volatile("bar.sync 1, 128;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
                 if (s_abort) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll 1
@@ -430,17 +440,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                     const uint64_t ph0_h = h ? ph0[1] : ph0[0];
                     const uint64_t pstep_h = h ? pstep[1] : pstep[0];
                     const bool has = 2 * P + h < U.nmt;
-                    float accf[FT];
+                    float accf[FH];
                     if (has) {
-                        const uint32_t tbase = taddr + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * kTcCols);
+                        const uint32_t tbase = taddr + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * kTcCols) + hcol;
                         float v[32];
                         // the angle of odd frequencies is the even one's rotated by one frequency step
                         float sr = 0.f, cr = 1.f, s1 = 0.f, c1 = 0.f;
                         if (live_h) sincos2pi_turns((uint32_t)(pstep_h >> 32), sr, cr);
 #pragma unroll
-                        for (int f = 0; f < FT; f++) {
+                        for (int fi = 0; fi < FH; fi++) {
+                            const int f = fh * FH + fi;       // FH is even: f and fi have the same parity
                             if (live_h) {
-                                if ((f & 1) == 0 || list) {
+                                if ((fi & 1) == 0 || list) {
                                     sincos2pi_turns((uint32_t)((ph0_h + tc_mult<LIST>(a, U, f) * pstep_h) >> 32), s1, c1);
                                 } else {
                                     const float cn = fmaf(c1, cr, -s1 * sr), sn = fmaf(s1, cr, c1 * sr);
@@ -452,14 +463,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                             float acc = 0.f;
 #pragma unroll
                             for (int n = 1; n <= NMAX; n++) {
-                                const int col = f * 2 * NMAX + 2 * (n - 1);
+                                const int col = fi * 2 * NMAX + 2 * (n - 1);   // relative to hcol
                                 if ((col & 31) == 0) tmem_ld32(tbase + col, v);
                                 acc = fmaf(an[n - 1], fmaf(v[col & 31], cp1, v[(col & 31) + 1] * sp1), acc);
                                 const float cn = fmaf(2.f * c1, cp1, -cp2), sn = fmaf(2.f * c1, sp1, -sp2);
                                 cp2 = cp1; sp2 = sp1;
                                 cp1 = cn; sp1 = sn;
                             }
-                            accf[f] = live_h ? acc : 0.f;
+                            accf[fi] = live_h ? acc : 0.f;
                         }
                     }
                     // release this accumulator (always, so the phases of both buffers advance per pair)
@@ -467,13 +478,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                     mbar_arrive(&bar_tempty[h]);
                     if (has) {
                         // sum over the 128 rows, fixed order
-                        const float x = warp_reduce_scatter<FT>(accf, lane);
-                        constexpr int SH = FT == 4 ? 3 : FT == 8 ? 2 : FT == 16 ? 1 : 0;
+                        const float x = warp_reduce_scatter<FH>(accf, lane);
+                        constexpr int SH = FH == 2 ? 4 : FH == 4 ? 3 : FH == 8 ? 2 : FH == 16 ? 1 : 0;
                         if ((lane & ((1 << SH) - 1)) == 0) s_red[ew][lane >> SH] = x;
-                        asm volatile("bar.sync 1, 128;" ::: "memory");
-                        if (ew == 0 && lane < FT)
-                            s_acc[lane] += ((s_red[0][lane] + s_red[1][lane]) + s_red[2][lane]) + s_red[3][lane];
-                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
+                        if (ew == 0 && lane < FT) {
+                            const int w0 = (lane / FH) * 4, fi = lane % FH;
+                            s_acc[lane] += ((s_red[w0][fi] + s_red[w0 + 1][fi]) + s_red[w0 + 2][fi]) + s_red[w0 + 3][fi];
+                        }
+                        asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
                     }
                 }
             }
@@ -512,12 +525,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tensor(const TensorArgs 
                     if (lane == 0 && key) atomicMax(a.best_key + U.c, key);
                 }
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
         }
         if (!ok && ew == 0 && lane == 0) atomicOr(a.status, 2);
     } else {
         // ---------------- Z producers: 256 threads ----------------
-        const int pt = tid - 6 * 32;                  // 0..255
+        const int pt = tid - (2 + EW) * 32;           // 0..255
         const int grp = pt / items;                   // stage group
         const int it = pt - grp * items;
         const int g = it & 7;                         // j-octet of the K chunk (fastest: conflict-free stores)
@@ -656,11 +669,11 @@ cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s)
 #define CP_TC_LAUNCH(NM)                                                                        \
     case NM:                                                                                    \
         if (list) {                                                                             \
-            if (bf) k_pair_tensor<NM, true, true><<<grid, kTcThreads, b, s>>>(a);               \
-            else k_pair_tensor<NM, false, true><<<grid, kTcThreads, b, s>>>(a);                 \
+            if (bf) k_pair_tensor<NM, true, true><<<grid, tc_threads(NM), b, s>>>(a);               \
+            else k_pair_tensor<NM, false, true><<<grid, tc_threads(NM), b, s>>>(a);                 \
         } else {                                                                                \
-            if (bf) k_pair_tensor<NM, true, false><<<grid, kTcThreads, b, s>>>(a);              \
-            else k_pair_tensor<NM, false, false><<<grid, kTcThreads, b, s>>>(a);                \
+            if (bf) k_pair_tensor<NM, true, false><<<grid, tc_threads(NM), b, s>>>(a);              \
+            else k_pair_tensor<NM, false, false><<<grid, tc_threads(NM), b, s>>>(a);                \
         }                                                                                       \
         break;
     switch (a.n_max) {
