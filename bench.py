@@ -38,6 +38,12 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 MUFU_EX2_PER_CLK_SM = 32      # measured sm_103a SFU ex2 rate (ex2 probe, 152 SMs)
+# DRAM bytes per byte of period-independent magnitude-kernel tiles, measured with
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum) on 256 curves x 2,048
+# frequencies: each tile is read from DRAM once per search, later units of the
+# same curve hit L2, so a full launch moves (this ratio) x (its tile bytes).
+DRAM_PER_W_BYTE_DIRECT = 1.037
+DRAM_PER_W_BYTE_TENSOR = 1.045
 
 
 def measured_peaks():
@@ -58,6 +64,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tuning", default=os.path.join(ROOT, "paper_1412_1840_gb300", "tuning_gb300.json"),
+                    help="autotuner table (paper_1412_1840_gb300.tune); 'none' for the built-in choices")
     ap.add_argument("--workload", default="ragged", choices=["ragged", "hierarchical", "bands", "single", "small", "throughput"])
     ap.add_argument("--n-curves", type=int, default=None)
     ap.add_argument("--form", default="direct", choices=["direct", "tensor"])
@@ -248,7 +256,11 @@ def main():
     td = torch.from_numpy(b.times).to(dev)
     md = torch.from_numpy(b.mags).to(dev)
     ed = torch.from_numpy(b.errs).to(dev)
-    tkw = dict(n_max=args.n_max, dtype=cp.CP_DTYPE_BF16 if args.dtype == "bf16" else cp.CP_DTYPE_FP16)
+    tuning = None
+    if args.tuning != "none" and os.path.exists(args.tuning):
+        tuning = cp.tuning_from(args.tuning)
+    tkw = dict(n_max=args.n_max, dtype=cp.CP_DTYPE_BF16 if args.dtype == "bf16" else cp.CP_DTYPE_FP16,
+               tuning=tuning)
     plan = cp.Plan(td, md, ed, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=form,
                    device=local, stream=stream.cuda_stream, **tkw)
     n = b.n_curves
@@ -299,7 +311,8 @@ def main():
     # ---- tensor-core form on the same resident batch ---------------------
     tensor = None
     if not args.no_tensor and args.form == "direct":
-        tkw2 = dict(n_max=args.n_max, dtype=cp.CP_DTYPE_BF16 if args.dtype == "bf16" else cp.CP_DTYPE_FP16)
+        tkw2 = dict(n_max=args.n_max, dtype=cp.CP_DTYPE_BF16 if args.dtype == "bf16" else cp.CP_DTYPE_FP16,
+                    tuning=tuning)
         tplan = cp.Plan(td, md, ed, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=cp.CP_FORM_TENSOR,
                         device=local, stream=stream.cuda_stream, **tkw2)
         tidx = np.empty(n, np.int64); tbf = np.empty(n, np.float64); tbs = np.empty(n, np.float32)
@@ -311,14 +324,15 @@ def main():
         te1 = [torch.cuda.Event(enable_timing=True) for _ in range(t_steps)]
         tk_ms = []
         barrier()
-        for k in range(t_steps):
-            flush.fill_(k & 0xff)
-            te0[k].record(stream)
-            tplan.best_period_into(tidx, tbf, tbs, tper, tps)
-            te1[k].record(stream)
-            ti = tplan.info()
-            tk_ms.append(ti["last_tensor_kernel_ms"])
-        barrier()
+        with ClockSampler(local) as tclk:
+            for k in range(t_steps):
+                flush.fill_(k & 0xff)
+                te0[k].record(stream)
+                tplan.best_period_into(tidx, tbf, tbs, tper, tps)
+                te1[k].record(stream)
+                ti = tplan.info()
+                tk_ms.append(ti["last_tensor_kernel_ms"])
+            barrier()
         t_total = max_over_ranks(sum(te0[k].elapsed_time(te1[k]) for k in range(t_steps)) / 1e3, device=dev)
         tplan.close()
         peaks = measured_peaks()
@@ -332,9 +346,11 @@ def main():
             "class_curves": dict(zip(["direct", "n4", "n8", "n16", "n32"], ti["class_curves"])),
             "best_idx_agreement_vs_direct": float(np.mean(tidx == idx)),
             "best_stat_max_rel_diff_vs_direct": float(rel.max()),
+            "clocks": tclk.summary(),
             "roofline": {"bound": "tensor", "achieved": tflops,
                          "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                         "frac": tflops / peaks["bf16_tflops_sustained"], "traffic": None,
+                         "frac": tflops / peaks["bf16_tflops_sustained"],
+                         "traffic": DRAM_PER_W_BYTE_TENSOR * ti["w_bytes_tensor"],
                          "kernel": "k_pair_tensor", "flops_basis": "2 N^2 n_max per curve-frequency (upper block "
                          "triangle of the 4 N^2 n_max dense GEMM)",
                          "peak_basis": "bf16 dense sustained, %s (fp16 has the same nominal rate)" % peaks["source"],
@@ -358,12 +374,13 @@ def main():
         "data": "synthetic",
         "config": {"workload": name, "form": args.form, "sigma_t": "Bowley-skewness rule",
                    "curves_per_gpu": n, "l2": "flushed between steps (256 MB write)",
+                   "tuning": os.path.basename(args.tuning) if tuning is not None else "built-in",
                    "parallelism": "independent curve batches per GPU"},
         "pair_freq_per_s": world * pf * args.steps / total_s,
         "gpu_launches": int(info["launches_per_search"]) * args.steps,
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gex2/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": DRAM_PER_W_BYTE_DIRECT * info["w_bytes_direct"],
                      "kernel": "k_pair_direct", "peak_basis": "32 MUFU ex2/clk/SM x %d SMs x 2070 MHz (max SM clock)"
                      % info["n_sm"], "avg_launch_ms": float(np.mean(pair_ms))},
         "clocks": clocks,
@@ -372,7 +389,8 @@ def main():
         peaks = measured_peaks()
         tflops = info["tensor_flops_search"] / (info["last_tensor_kernel_ms"] / 1e3) / 1e12
         line["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": peaks["bf16_tflops_sustained"],
-                            "unit": "TFLOP/s", "frac": tflops / peaks["bf16_tflops_sustained"], "traffic": None,
+                            "unit": "TFLOP/s", "frac": tflops / peaks["bf16_tflops_sustained"],
+                            "traffic": DRAM_PER_W_BYTE_TENSOR * info["w_bytes_tensor"],
                             "kernel": "k_pair_tensor", "peak_basis": "bf16 dense sustained, " + peaks["source"],
                             "avg_launch_ms": float(info["last_tensor_kernel_ms"])}
     if tensor is not None:

@@ -105,6 +105,29 @@ typedef struct {
     int32_t trials_per_band;         /* bands method: N_t in [1, CP_BANDS_MAX_TRIALS]  */
 } cp_freq_grid;
 
+/*
+ * Tuned launch choices (written by the package's autotuner from timings on
+ * the target GPU; not part of the method).  Curves are grouped in buckets by
+ * N: bucket b holds bucket_max_n[b-1] < N <= bucket_max_n[b].  For a curve
+ * in bucket b:
+ *   direct_fc[b]       frequencies per work unit of the direct form (2, 4, 8
+ *                      or 16; lowered to the largest that fits the kernel's
+ *                      shared trig table for the curve's N);
+ *   tensor_classes[b]  with n_max = 0, bit k set lets the harmonic class
+ *                      8 << k (8, 16, 32) run in the tensor form; a curve whose
+ *                      class bit is clear runs in the direct form.
+ * Curves above the last bucket, and plans without tuning, use the built-in
+ * choices (16 frequencies per unit where they fit; every class in the tensor
+ * form).  Results never depend on the tuning beyond the form's own rounding.
+ */
+#define CP_TUNE_MAX_BUCKETS 16
+typedef struct {
+    int32_t n_buckets;                              /* 0..CP_TUNE_MAX_BUCKETS        */
+    int32_t bucket_max_n[CP_TUNE_MAX_BUCKETS];      /* strictly ascending, >= 2      */
+    int32_t direct_fc[CP_TUNE_MAX_BUCKETS];
+    int32_t tensor_classes[CP_TUNE_MAX_BUCKETS];
+} cp_tuning;
+
 typedef struct {
     int32_t sigma_t_mode;            /* CP_SIGMA_T_*                                    */
     float sigma_t;                   /* fixed kernel size (mode FIXED)                  */
@@ -120,10 +143,11 @@ typedef struct {
     int32_t input_memory;            /* CP_MEM_HOST or CP_MEM_DEVICE                    */
     int32_t use_graph;               /* capture cp_best_period's step in a CUDA graph   */
     int32_t device;                  /* CUDA device ordinal                             */
+    const cp_tuning *tuning;         /* host, copied by cp_plan; NULL = built-in choices */
 } cp_options;
 
 /* Fills defaults: FIXED sigma_t = 0.3, alpha = 1, DIRECT form, FP16,
- * n_max = 0, HOST inputs, graphs on, device 0. */
+ * n_max = 0, HOST inputs, graphs on, device 0, no tuning. */
 void cp_default_options(cp_options *opt);
 
 /*
@@ -225,6 +249,8 @@ typedef struct {
     float reserved0;
     double window_terms_search;   /* bands method: spectral-window terms (band point x  */
                                   /* grid frequency) of one cp_best_period              */
+    double w_bytes_direct;        /* bytes of the magnitude-kernel tiles one search     */
+    double w_bytes_tensor;        /* builds for the direct / tensor-form curves         */
 } cp_plan_info;
 
 cp_status cp_get_plan_info(cp_plan_t plan, cp_plan_info *info);

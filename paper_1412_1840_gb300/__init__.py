@@ -44,11 +44,39 @@ class cp_freq_grid(ctypes.Structure):
                 ("n_bands", ctypes.c_int32), ("trials_per_band", ctypes.c_int32)]
 
 
+CP_TUNE_MAX_BUCKETS = 16
+
+
+class cp_tuning(ctypes.Structure):
+    _fields_ = [("n_buckets", ctypes.c_int32), ("bucket_max_n", ctypes.c_int32 * CP_TUNE_MAX_BUCKETS),
+                ("direct_fc", ctypes.c_int32 * CP_TUNE_MAX_BUCKETS),
+                ("tensor_classes", ctypes.c_int32 * CP_TUNE_MAX_BUCKETS)]
+
+
+def tuning_from(table) -> cp_tuning:
+    """cp_tuning from the autotuner's JSON table (a path or the loaded dict)."""
+    if isinstance(table, (str, os.PathLike)):
+        import json
+        with open(table) as fh:
+            table = json.load(fh)
+    t = cp_tuning()
+    buckets = table["buckets"]
+    if len(buckets) > CP_TUNE_MAX_BUCKETS:
+        raise ValueError("at most %d buckets" % CP_TUNE_MAX_BUCKETS)
+    t.n_buckets = len(buckets)
+    for i, bk in enumerate(buckets):
+        t.bucket_max_n[i] = int(bk["max_n"])
+        t.direct_fc[i] = int(bk["direct_fc"])
+        t.tensor_classes[i] = sum(1 << k for k, cl in enumerate(("8", "16", "32")) if bk["tensor"].get(cl, True))
+    return t
+
+
 class cp_options(ctypes.Structure):
     _fields_ = [("sigma_t_mode", ctypes.c_int32), ("sigma_t", ctypes.c_float),
                 ("sigma_t_per_curve", ctypes.POINTER(ctypes.c_float)), ("alpha", ctypes.c_float),
                 ("form", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n_max", ctypes.c_int32),
-                ("input_memory", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("input_memory", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("tuning", ctypes.POINTER(cp_tuning))]
 
 
 class cp_plan_info(ctypes.Structure):
@@ -59,7 +87,8 @@ class cp_plan_info(ctypes.Structure):
                 ("last_tensor_kernel_ms", ctypes.c_float), ("last_direct_kernel_ms", ctypes.c_float),
                 ("tensor_flops_search", ctypes.c_double), ("direct_pair_freq_search", ctypes.c_double),
                 ("last_bands_kernel_ms", ctypes.c_float), ("reserved0", ctypes.c_float),
-                ("window_terms_search", ctypes.c_double)]
+                ("window_terms_search", ctypes.c_double), ("w_bytes_direct", ctypes.c_double),
+                ("w_bytes_tensor", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -168,7 +197,7 @@ class Plan:
 
     def __init__(self, times, mags, errs, offsets, grid: cp_freq_grid, sigma_t=0.3, sigma_t_mode=None,
                  sigma_t_per_curve=None, alpha=1.0, form=CP_FORM_DIRECT, dtype=CP_DTYPE_FP16, n_max=0,
-                 use_graph=True, device=None, stream=None):
+                 use_graph=True, device=None, stream=None, tuning=None):
         L = _load()
         pt, dev_t, kt = _ptr(times)
         pm, dev_m, km = _ptr(mags)
@@ -192,6 +221,10 @@ class Plan:
         o.n_max = int(n_max)
         o.input_memory = CP_MEM_DEVICE if dev_t else CP_MEM_HOST
         o.use_graph = 1 if use_graph else 0
+        if tuning is not None:
+            tt = tuning if isinstance(tuning, cp_tuning) else tuning_from(tuning)
+            self._keep.append(tt)
+            o.tuning = ctypes.pointer(tt)
         if device is None:
             device = times.device.index if dev_t and times.device.index is not None else 0
         o.device = int(device)

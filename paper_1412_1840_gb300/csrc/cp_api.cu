@@ -273,12 +273,22 @@ cp_status plan_sigma_t(cp_plan_t p, const cp_options& opt, std::vector<float>& s
 // outside capture the flag is not allowed.
 unsigned rec_flags(cp_plan_t p) { return p->capturing ? cudaEventRecordExternal : cudaEventRecordDefault; }
 
-int fc_for(int n)
+// Frequencies per direct-form unit: the requested count (16 by default),
+// halved until the unit's trig table fits the kernel's shared-memory budget.
+int fc_for(int n, int want = kFcMax)
 {
     const int npad = (n + kTile - 1) / kTile * kTile;
-    int f = kFcMax;
+    int f = want;
     while (f > 2 && (size_t)npad * f * 12 > (size_t)kTableBytes) f >>= 1;
     return f;
+}
+
+// Tuning bucket of a curve of n samples, or -1 (built-in choices).
+int tune_bucket(const cp_tuning& t, int n)
+{
+    for (int b = 0; b < t.n_buckets; b++)
+        if (n <= t.bucket_max_n[b]) return b;
+    return -1;
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -639,6 +649,7 @@ void cp_default_options(cp_options* o)
     o->input_memory = CP_MEM_HOST;
     o->use_graph = 1;
     o->device = 0;
+    o->tuning = nullptr;
 }
 
 int64_t cp_max_points(void) { return kMaxN; }
@@ -712,6 +723,22 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         return fail(CP_EINVAL, "cp_plan: alpha must be finite and > 0");
     if (opt.input_memory != CP_MEM_HOST && opt.input_memory != CP_MEM_DEVICE)
         return fail(CP_EINVAL, "cp_plan: input_memory must be CP_MEM_HOST or CP_MEM_DEVICE");
+    cp_tuning tune{};
+    if (opt.tuning) {
+        tune = *opt.tuning;
+        if (tune.n_buckets < 0 || tune.n_buckets > CP_TUNE_MAX_BUCKETS)
+            return fail(CP_EINVAL, "cp_plan: tuning.n_buckets must be in [0, CP_TUNE_MAX_BUCKETS]");
+        for (int b = 0; b < tune.n_buckets; b++) {
+            const int fc = tune.direct_fc[b];
+            if (tune.bucket_max_n[b] < 2 || (b > 0 && tune.bucket_max_n[b] <= tune.bucket_max_n[b - 1]))
+                return fail(CP_EINVAL, "cp_plan: tuning.bucket_max_n must be >= 2 and strictly ascending");
+            if (fc != 2 && fc != 4 && fc != 8 && fc != 16)
+                return fail(CP_EINVAL, "cp_plan: tuning.direct_fc must be 2, 4, 8 or 16");
+            if (tune.tensor_classes[b] < 0 || tune.tensor_classes[b] > 7)
+                return fail(CP_EINVAL, "cp_plan: tuning.tensor_classes must be a 3-bit mask");
+        }
+        opt.tuning = nullptr;   // copied; the caller's struct is not kept
+    }
     const cp_freq_grid g = *grid;
     if (!(std::isfinite(g.f_min) && g.f_min >= 0.0 && std::isfinite(g.df) && g.df > 0.0))
         return fail(CP_EINVAL, "cp_plan: need finite f_min >= 0 and df > 0");
@@ -769,7 +796,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             return fail(CP_EUNSUPPORTED, "cp_plan: curve " + std::to_string(c) + " has " + std::to_string(n) +
                                              " samples; the maximum is " + std::to_string(kMaxN));
         max_n = std::max(max_n, (int)n);
-        p->fc[c] = fc_for((int)n);
+        const int tb = tune_bucket(tune, (int)n);
+        p->fc[c] = fc_for((int)n, tb >= 0 ? tune.direct_fc[tb] : kFcMax);
     }
     p->max_band_points = (max_n + 9) / 10;   // a band holds at most ceil(N/10) samples
     p->n_points = offsets[n_curves];
@@ -823,7 +851,13 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             std::vector<float> st((size_t)n_curves);
             cp_status s2 = plan_sigma_t(p, opt, st);
             if (s2 != CP_OK) return s2;
-            for (int64_t c = 0; c < n_curves; c++) p->cls[c] = harmonics_for(st[c]);
+            for (int64_t c = 0; c < n_curves; c++) {
+                int cl = harmonics_for(st[c]);
+                const int tb = tune_bucket(tune, (int)(offsets[c + 1] - offsets[c]));
+                const int bit = cl == 8 ? 1 : cl == 16 ? 2 : cl == 32 ? 4 : 0;
+                if (tb >= 0 && bit && !(tune.tensor_classes[tb] & bit)) cl = 0;   // tuned: direct form is faster here
+                p->cls[c] = cl;
+            }
         }
     }
     for (int64_t c = 0; c < n_curves; c++) p->class_count[class_rank(p->cls[c])]++;
@@ -1213,6 +1247,11 @@ cp_status cp_get_plan_info(cp_plan_t p, cp_plan_info* info)
     info->last_bands_kernel_ms = p->last_bands_ms;
     info->reserved0 = 0.f;
     info->window_terms_search = p->window_terms;
+    double wd = 0, wt = 0;
+    for (const Wave& w : p->waves)
+        (w.cls ? wt : wd) += (double)(w.tile_end - w.tile_begin) * (w.cls ? 128.0 * 64 * 2 : (double)kTileFloats * 4);
+    info->w_bytes_direct = wd;
+    info->w_bytes_tensor = wt;
     return CP_OK;
 }
 

@@ -45,7 +45,7 @@ def _c_layout(struct, fields):
 
 
 @pytest.mark.parametrize("cls,name", [(cp.cp_freq_grid, "cp_freq_grid"), (cp.cp_options, "cp_options"),
-                                      (cp.cp_plan_info, "cp_plan_info")])
+                                      (cp.cp_plan_info, "cp_plan_info"), (cp.cp_tuning, "cp_tuning")])
 def test_binding_structs_match_header_layout(cls, name):
     fields = [f for f, _ in cls._fields_]
     got = _c_layout(name, fields)
@@ -108,6 +108,16 @@ def test_argument_validation_precedes_device_use():
     g = cp.make_grid(0.01, 0.01, 10)
     g.hierarchical = 3
     assert _plan_status([0, 5], grid=g) == cp.CP_EINVAL
+    good = {"buckets": [{"max_n": 256, "direct_fc": 16, "tensor": {"8": True, "16": True, "32": False}},
+                        {"max_n": 4096, "direct_fc": 4, "tensor": {}}]}
+    t = cp.tuning_from(good)
+    assert t.n_buckets == 2 and list(t.tensor_classes[:2]) == [3, 7]
+    bad_fc = cp.tuning_from(good); bad_fc.direct_fc[0] = 6
+    assert _plan_status([0, 5], tuning=bad_fc) == cp.CP_EINVAL
+    bad_order = cp.tuning_from(good); bad_order.bucket_max_n[1] = 100
+    assert _plan_status([0, 5], tuning=bad_order) == cp.CP_EINVAL
+    bad_mask = cp.tuning_from(good); bad_mask.tensor_classes[0] = 9
+    assert _plan_status([0, 5], tuning=bad_mask) == cp.CP_EINVAL
 
 
 def test_no_device_is_an_error_not_a_fallback():

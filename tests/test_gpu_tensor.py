@@ -167,3 +167,25 @@ def test_tensor_auto_harmonics_per_curve():
     err = peak_err(out, ref, range(b.n_curves))
     assert np.all(err <= TOL), err
     accept_best(best, ref, range(b.n_curves), TOL)
+
+
+def test_tuning_table_moves_a_class_to_the_direct_form():
+    """A tuning table that disables the 16-harmonic tensor class for N <= 400
+    sends exactly those curves to the direct form; all curves still meet the
+    tensor tolerance against the oracle."""
+    b = synth.ragged_batch(12, seed=35, n_lo=150, n_hi=650)
+    st = np.full(b.n_curves, 0.3, np.float32)           # 16 harmonics by the tail rule
+    g = synth.Grid(0.01, 2e-4, 700)
+    table = {"buckets": [{"max_n": 400, "direct_fc": 8, "tensor": {"8": True, "16": False, "32": True}}]}
+    with cp.Plan(b.times, b.mags, b.errs, b.offsets, cp.grid_from(g), sigma_t_per_curve=st,
+                 form=cp.CP_FORM_TENSOR, n_max=0, tuning=table) as p:
+        out = torch.empty((b.n_curves, g.n_freq), dtype=torch.float32, device="cuda")
+        p.periodogram(out)
+        p.sync()
+        info = p.info()
+    small = int(np.sum(b.sizes <= 400))
+    assert 0 < small < b.n_curves
+    assert info["class_curves"] == [small, 0, 0, b.n_curves - small, 0]
+    ref = oracle.batch_nckp(b, st.astype(np.float64), g.freqs())
+    err = peak_err(out.cpu().numpy(), ref, range(b.n_curves))
+    assert np.all(err <= TOL), err
