@@ -42,6 +42,11 @@ class OrcOptions(ctypes.Structure):
                 ("alpha", D)]
 
 
+class OrcPrep(ctypes.Structure):
+    _fields_ = [("n_in", I64), ("n_out", I64), ("kept", ctypes.c_int), ("detrended", ctypes.c_int),
+                ("e_mean", D), ("e_std", D), ("a0", D), ("a1", D), ("r", D)]
+
+
 class OrcResult(ctypes.Structure):
     _fields_ = [("best_idx", I64), ("best_freq", D), ("best_stat", D), ("is_periodic", ctypes.c_int),
                 ("psnr", D), ("sigma_y", D), ("sigma_t", D), ("ip", D)]
@@ -85,6 +90,11 @@ def lib():
                                      ctypes.POINTER(OrcOptions), ctypes.POINTER(OrcResult)]
         L.orc_batch_nckp.restype = None
         L.orc_batch_nckp.argtypes = [PD, PF, PF, PI64, I64, PD, PD, I64, PD]
+        L.orc_chi2_line.restype = None; L.orc_chi2_line.argtypes = [PD, PD, PD, I64, PD, PD]
+        L.orc_pearson.restype = D; L.orc_pearson.argtypes = [PD, PD, I64]
+        L.orc_preprocess.restype = OrcPrep; L.orc_preprocess.argtypes = [PD, PD, PD, I64, I64, PD, PD, PD]
+        L.orc_batch_preprocess.restype = None
+        L.orc_batch_preprocess.argtypes = [PD, PF, PF, PI64, I64, I64, PD, PD, PD, PI64, ctypes.POINTER(OrcPrep)]
         L.orc_bands_of.restype = None; L.orc_bands_of.argtypes = [PD, I64, PI32]
         L.orc_band_derivative_sums.restype = None
         L.orc_band_derivative_sums.argtypes = [PD, PD, I64, PI32, PD]
@@ -167,6 +177,53 @@ def top_local_maxima(v, top_k) -> np.ndarray:
     v, pv = _d(v); out = np.zeros(max(int(top_k), 1), dtype=np.int64)
     n = lib().orc_top_local_maxima(pv, v.shape[0], int(top_k), out.ctypes.data_as(PI64))
     return out[:n]
+
+
+# ---- preprocessing, Section 5.1 --------------------------------------------
+
+
+def chi2_line(t, x, e):
+    t, pt = _d(t); x, px = _d(x); e, pe = _d(e); a0 = D(); a1 = D()
+    lib().orc_chi2_line(pt, px, pe, t.shape[0], ctypes.byref(a0), ctypes.byref(a1))
+    return a0.value, a1.value
+
+
+def pearson(u, v) -> float:
+    u, pu = _d(u); v, pv = _d(v)
+    return lib().orc_pearson(pu, pv, u.shape[0])
+
+
+def _prep_dict(r):
+    return {k: getattr(r, k) for k, _ in OrcPrep._fields_}
+
+
+def preprocess(t, x, e, min_n=50):
+    """One curve: (kept t, x, e arrays, summary dict)."""
+    t, pt = _d(t); x, px = _d(x); e, pe = _d(e)
+    n = t.shape[0]
+    ot, ox, oe = np.empty(max(n, 1)), np.empty(max(n, 1)), np.empty(max(n, 1))
+    r = lib().orc_preprocess(pt, px, pe, n, int(min_n), ot.ctypes.data_as(PD), ox.ctypes.data_as(PD),
+                             oe.ctypes.data_as(PD))
+    k = r.n_out
+    return ot[:k], ox[:k], oe[:k], _prep_dict(r)
+
+
+def batch_preprocess(batch, min_n=50):
+    """CSR batch -> (times, mags, errs as float64, out_offsets over the input curves, list of summaries)."""
+    t = np.ascontiguousarray(batch.times, np.float64)
+    m = np.ascontiguousarray(batch.mags, np.float32)
+    e = np.ascontiguousarray(batch.errs, np.float32)
+    off = np.ascontiguousarray(batch.offsets, np.int64)
+    nc = off.shape[0] - 1
+    n = max(int(off[-1]), 1)
+    ot, ox, oe = np.empty(n), np.empty(n), np.empty(n)
+    oo = np.empty(nc + 1, np.int64)
+    res = (OrcPrep * max(nc, 1))()
+    lib().orc_batch_preprocess(t.ctypes.data_as(PD), m.ctypes.data_as(PF), e.ctypes.data_as(PF),
+                               off.ctypes.data_as(PI64), nc, int(min_n), ot.ctypes.data_as(PD),
+                               ox.ctypes.data_as(PD), oe.ctypes.data_as(PD), oo.ctypes.data_as(PI64), res)
+    k = int(oo[-1])
+    return ot[:k], ox[:k], oe[:k], oo, [_prep_dict(res[c]) for c in range(nc)]
 
 
 # ---- bands method, Section 3.1 ---------------------------------------------

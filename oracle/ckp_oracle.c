@@ -39,7 +39,12 @@
  *     floor((k+1)N/10)) (ties by sample index); bands ordered by D_j
  *     descending, ties to the lower band; one-day frequencies keep their
  *     values in the local-maximum test and are only skipped as candidates;
- *     a one-sample band's window is exactly 1; missing entries are -1.
+ *     a one-sample band's window is exactly 1; missing entries are -1;
+ *   preprocessing: std(e) is the population standard deviation; the cut is
+ *     strict (e_i < mean + 3 std); chi^2 weights 1/e_i^2; the correlation is
+ *     the unweighted Pearson coefficient between the kept magnitudes and the
+ *     fitted line; the whole fit a0 + a1 t (intercept included) is removed;
+ *     the sample order of the kept points is preserved.
  */
 #include <math.h>
 #include <stdint.h>
@@ -608,5 +613,126 @@ void orc_batch_bands_trials(const double *times, const float *mags, const int64_
             y[i] = (double)mags[a + i];
         orc_bands_trials(times + a, y, n, f_min, df, nk, n_bands, n_t, out_k + c * n_bands * n_t);
         free(y);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Preprocessing, Section 5.1                                              */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t n_in, n_out;     /* samples before / after the error-bar cut          */
+    int kept;                /* n_out >= 50                                       */
+    int detrended;           /* fit removed (corr > 0.5)                          */
+    double e_mean, e_std;    /* of the input error bars                           */
+    double a0, a1, r;        /* chi^2 fit x = a0 + a1 t and its correlation        */
+} orc_prep;
+
+/* Eq. (chisquare): minimise sum (a0 + a1 t_i - x_i)^2 / e_i^2 by its normal
+ * equations (derivatives wrt a0 and a1 set to zero), solved by Cramer's rule. */
+void orc_chi2_line(const double *t, const double *x, const double *e, int64_t n, double *a0, double *a1)
+{
+    double S = 0, St = 0, Sx = 0, Stt = 0, Stx = 0;
+    for (int64_t i = 0; i < n; i++) {
+        double w = 1.0 / (e[i] * e[i]);
+        S += w;
+        St += w * t[i];
+        Sx += w * x[i];
+        Stt += w * t[i] * t[i];
+        Stx += w * t[i] * x[i];
+    }
+    double det = S * Stt - St * St;
+    *a1 = (S * Stx - St * Sx) / det;
+    *a0 = (Stt * Sx - St * Stx) / det;
+}
+
+/* Pearson correlation coefficient of two sequences (0 when either is constant). */
+double orc_pearson(const double *u, const double *v, int64_t n)
+{
+    double mu = 0, mv = 0;
+    for (int64_t i = 0; i < n; i++) {
+        mu += u[i];
+        mv += v[i];
+    }
+    mu /= (double)n;
+    mv /= (double)n;
+    double suv = 0, suu = 0, svv = 0;
+    for (int64_t i = 0; i < n; i++) {
+        suv += (u[i] - mu) * (v[i] - mv);
+        suu += (u[i] - mu) * (u[i] - mu);
+        svv += (v[i] - mv) * (v[i] - mv);
+    }
+    if (suu == 0.0 || svv == 0.0)
+        return 0.0;
+    return suv / sqrt(suu * svv);
+}
+
+/* One curve: error-bar cut, size check, chi^2 detrend.  Writes the kept
+ * samples (in their order) to out_t, out_x, out_e (detrended x when the fit
+ * is removed) and returns the summary.  min_n = 50 in the paper. */
+orc_prep orc_preprocess(const double *t, const double *x, const double *e, int64_t n, int64_t min_n,
+                        double *out_t, double *out_x, double *out_e)
+{
+    orc_prep r;
+    memset(&r, 0, sizeof(r));
+    r.n_in = n;
+    double m = 0;
+    for (int64_t i = 0; i < n; i++)
+        m += e[i];
+    m /= (double)n;
+    double v = 0;
+    for (int64_t i = 0; i < n; i++)
+        v += (e[i] - m) * (e[i] - m);
+    r.e_mean = m;
+    r.e_std = sqrt(v / (double)n);
+    double cut = r.e_mean + 3.0 * r.e_std;
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; i++)
+        if (e[i] < cut) {
+            out_t[k] = t[i];
+            out_x[k] = x[i];
+            out_e[k] = e[i];
+            k++;
+        }
+    r.n_out = k;
+    r.kept = k >= min_n;
+    if (k < 2)
+        return r;
+    orc_chi2_line(out_t, out_x, out_e, k, &r.a0, &r.a1);
+    double *fit = (double *)malloc((size_t)k * sizeof(double));
+    for (int64_t i = 0; i < k; i++)
+        fit[i] = r.a0 + r.a1 * out_t[i];
+    r.r = orc_pearson(out_x, fit, k);
+    if (r.r > 0.5) {
+        r.detrended = 1;
+        for (int64_t i = 0; i < k; i++)
+            out_x[i] -= fit[i];
+    }
+    free(fit);
+    return r;
+}
+
+/* Batch driver: CSR in (times f64, mags / errs f32 widened exactly), CSR out
+ * of the kept curves' samples (out_offsets over the input curves: curve c's
+ * kept samples at [out_offsets[c], out_offsets[c+1]) when kept, empty when
+ * discarded), summaries per input curve. */
+void orc_batch_preprocess(const double *times, const float *mags, const float *errs, const int64_t *offsets,
+                          int64_t n_curves, int64_t min_n, double *out_t, double *out_x, double *out_e,
+                          int64_t *out_offsets, orc_prep *res)
+{
+    out_offsets[0] = 0;
+    for (int64_t c = 0; c < n_curves; c++) {
+        int64_t a = offsets[c], n = offsets[c + 1] - offsets[c];
+        double *x = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+        double *e = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+        for (int64_t i = 0; i < n; i++) {
+            x[i] = (double)mags[a + i];
+            e[i] = (double)errs[a + i];
+        }
+        int64_t o = out_offsets[c];
+        res[c] = orc_preprocess(times + a, x, e, n, min_n, out_t + o, out_x + o, out_e + o);
+        out_offsets[c + 1] = o + (res[c].kept ? res[c].n_out : 0);
+        free(x);
+        free(e);
     }
 }
