@@ -95,6 +95,8 @@ def lib():
         L.orc_preprocess.restype = OrcPrep; L.orc_preprocess.argtypes = [PD, PD, PD, I64, I64, PD, PD, PD]
         L.orc_batch_preprocess.restype = None
         L.orc_batch_preprocess.argtypes = [PD, PF, PF, PI64, I64, I64, PD, PD, PD, PI64, ctypes.POINTER(OrcPrep)]
+        L.orc_whiten.restype = None; L.orc_whiten.argtypes = [PD, PD, I64, D, I64, PD]
+        L.orc_batch_whiten.restype = None; L.orc_batch_whiten.argtypes = [PD, PF, PI64, I64, PD, I64, PD]
         L.orc_bands_of.restype = None; L.orc_bands_of.argtypes = [PD, I64, PI32]
         L.orc_band_derivative_sums.restype = None
         L.orc_band_derivative_sums.argtypes = [PD, PD, I64, PI32, PD]
@@ -224,6 +226,26 @@ def batch_preprocess(batch, min_n=50):
                                ox.ctypes.data_as(PD), oe.ctypes.data_as(PD), oo.ctypes.data_as(PI64), res)
     k = int(oo[-1])
     return ot[:k], ox[:k], oe[:k], oo, [_prep_dict(res[c]) for c in range(nc)]
+
+
+# ---- whitening, Section 7.1 -------------------------------------------------
+
+
+def whiten(t, x, p0, w=30) -> np.ndarray:
+    t, pt = _d(t); x, px = _d(x); out = np.empty(t.shape[0])
+    lib().orc_whiten(pt, px, t.shape[0], float(p0), int(w), out.ctypes.data_as(PD))
+    return out
+
+
+def batch_whiten(batch, p0, w=30) -> np.ndarray:
+    t = np.ascontiguousarray(batch.times, np.float64)
+    m = np.ascontiguousarray(batch.mags, np.float32)
+    off = np.ascontiguousarray(batch.offsets, np.int64)
+    p = np.ascontiguousarray(p0, np.float64)
+    out = np.empty(max(int(off[-1]), 1))
+    lib().orc_batch_whiten(t.ctypes.data_as(PD), m.ctypes.data_as(PF), off.ctypes.data_as(PI64), off.shape[0] - 1,
+                           p.ctypes.data_as(PD), int(w), out.ctypes.data_as(PD))
+    return out[:int(off[-1])]
 
 
 # ---- bands method, Section 3.1 ---------------------------------------------

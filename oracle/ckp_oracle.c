@@ -44,7 +44,11 @@
  *     strict (e_i < mean + 3 std); chi^2 weights 1/e_i^2; the correlation is
  *     the unweighted Pearson coefficient between the kept magnitudes and the
  *     fitted line; the whole fit a0 + a1 t (intercept included) is removed;
- *     the sample order of the kept points is preserved.
+ *     the sample order of the kept points is preserved;
+ *   whitening: phase = frac(t / P0); folded order by phase, equal phases by
+ *     sample index; the moving average is circular over the folded curve
+ *     (the fold is periodic), window of w = min(30, N) samples covering
+ *     folded positions k - w/2 .. k - w/2 + w - 1.
  */
 #include <math.h>
 #include <stdint.h>
@@ -734,5 +738,62 @@ void orc_batch_preprocess(const double *times, const float *mags, const float *e
         out_offsets[c + 1] = o + (res[c].kept ? res[c].n_out : 0);
         free(x);
         free(e);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Whitening, Section 7.1                                                  */
+/* ---------------------------------------------------------------------- */
+
+typedef struct { double ph; int64_t i; } orc_phase_item;
+
+static int cmp_phase_item(const void *a, const void *b)
+{
+    const orc_phase_item *x = (const orc_phase_item *)a, *z = (const orc_phase_item *)b;
+    if (x->ph < z->ph) return -1;
+    if (x->ph > z->ph) return 1;
+    return (x->i > z->i) - (x->i < z->i);
+}
+
+/* Steps 1-4: fold at p0, template = moving average of w folded samples,
+ * subtract it, samples back in time order (out[i] for input sample i). */
+void orc_whiten(const double *t, const double *x, int64_t n, double p0, int64_t w, double *out)
+{
+    orc_phase_item *f = (orc_phase_item *)malloc((size_t)(n > 0 ? n : 1) * sizeof(orc_phase_item));
+    for (int64_t i = 0; i < n; i++) {
+        double q = t[i] / p0;
+        f[i].ph = q - floor(q);
+        f[i].i = i;
+    }
+    qsort(f, (size_t)n, sizeof(orc_phase_item), cmp_phase_item);
+    if (w > n)
+        w = n;
+    for (int64_t k = 0; k < n; k++) {
+        double acc = 0.0;
+        for (int64_t j = 0; j < w; j++) {
+            int64_t q = k - w / 2 + j;
+            q = ((q % n) + n) % n;
+            acc += x[f[q].i];
+        }
+        out[f[k].i] = x[f[k].i] - acc / (double)w;
+    }
+    free(f);
+}
+
+/* Batch driver: one period per curve (p0 <= 0 or non-finite: copied unchanged). */
+void orc_batch_whiten(const double *times, const float *mags, const int64_t *offsets, int64_t n_curves,
+                      const double *p0, int64_t w, double *out)
+{
+    for (int64_t c = 0; c < n_curves; c++) {
+        int64_t a = offsets[c], n = offsets[c + 1] - offsets[c];
+        double *x = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+        for (int64_t i = 0; i < n; i++)
+            x[i] = (double)mags[a + i];
+        if (p0[c] > 0.0 && isfinite(p0[c]))
+            orc_whiten(times + a, x, n, p0[c], w, out + a);
+        else
+            for (int64_t i = 0; i < n; i++)
+                out[a + i] = x[i];
+        free(x);
     }
 }
