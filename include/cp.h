@@ -226,6 +226,45 @@ cp_status cp_curve_stats(cp_plan_t plan, float *sigma_y, float *sigma_t, double 
  */
 cp_status cp_trial_frequencies(cp_plan_t plan, int32_t *trial_idx, float *trial_stat);
 
+/*
+ * cp_preprocess -- the cleaning of Section 5.1 on the device, for a batch
+ * before it is planned: samples whose error bar is not below
+ * mean(e) + 3 std(e) (population std, per curve) are dropped; curves with
+ * fewer than min_n samples left (50 in the paper) are discarded; the
+ * weighted linear fit of Eq. (chisquare), x = a0 + a1 t with weights
+ * 1/e^2, is subtracted (intercept included) when the Pearson correlation
+ * of the kept magnitudes with the fit exceeds 0.5.  Kept samples keep
+ * their order.  Statistics in FP64.
+ *   times, mags, errs        DEVICE input CSR arrays (offsets[n_curves] samples)
+ *   offsets                  HOST, n_curves + 1, offsets[0] = 0, curves of 1..cp_max_points()
+ *   out_times, out_mags, out_errs  DEVICE, room for offsets[n_curves] samples;
+ *                            the kept samples of the kept curves, curve by curve
+ *   out_offsets              HOST, n_curves + 1: curve c's kept samples are at
+ *                            [out_offsets[c], out_offsets[c+1]); empty when discarded
+ *   flags                    HOST, n_curves or NULL: bit 0 kept, bit 1 fit removed
+ *   fit                      HOST, 3 * n_curves or NULL: a0, a1, correlation
+ * Synchronous on cuda_stream (the output offsets need the kept counts);
+ * allocates and frees small temporaries.
+ */
+cp_status cp_preprocess(const double *times, const float *mags, const float *errs, const int64_t *offsets,
+                        int64_t n_curves, int32_t min_n, double *out_times, float *out_mags, float *out_errs,
+                        int64_t *out_offsets, uint8_t *flags, double *fit, void *cuda_stream);
+
+/*
+ * cp_whiten -- the whitening of Section 7.1 (multimodes) on the device: each
+ * curve is folded at its period p0[c] (phase = frac(t / p0), equal phases in
+ * sample order), a template is taken as the circular moving average of
+ * w = min(window, N) folded samples (30 in the paper; folded positions
+ * k - w/2 .. k - w/2 + w - 1), subtracted, and the samples are returned in
+ * their original order.  A curve with p0[c] <= 0 or not finite is copied.
+ *   times, mags, out_mags    DEVICE CSR arrays; out_mags may equal mags
+ *   offsets, p0              HOST, n_curves + 1 and n_curves entries
+ * Synchronous on cuda_stream.  Searching the whitened curves (a plan bound to
+ * out_mags) gives the second mode P1.
+ */
+cp_status cp_whiten(const double *times, const float *mags, const int64_t *offsets, int64_t n_curves,
+                    const double *p0, int32_t window, float *out_mags, void *cuda_stream);
+
 /* Work and timing of the plan (for throughput and roofline reports). */
 typedef struct {
     int64_t n_curves;

@@ -8,7 +8,7 @@ library cannot be loaded or no CUDA device is present, calls raise.
 Entry points carry the C names: ``cp_plan``, ``cp_periodogram``,
 ``cp_best_period``, ``cp_sync``, ``cp_curve_stats``, ``cp_get_plan_info``,
 ``cp_destroy``, ``cp_bessel_coefficients``, ``cp_max_points``,
-``cp_trial_frequencies``.  ``Plan`` wraps
+``cp_trial_frequencies``, ``cp_preprocess``, ``cp_whiten``.  ``Plan`` wraps
 a plan handle and keeps the bound input arrays alive.
 """
 from __future__ import annotations
@@ -117,6 +117,8 @@ def _load():
         L.cp_curve_stats.argtypes = [vp, vp, vp, vp, vp]
         L.cp_get_plan_info.argtypes = [vp, ctypes.POINTER(cp_plan_info)]
         L.cp_trial_frequencies.argtypes = [vp, vp, vp]
+        L.cp_preprocess.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp]
+        L.cp_whiten.argtypes = [vp, vp, vp, i64, vp, ctypes.c_int32, vp, vp]
         L.cp_destroy.argtypes = [vp]
         L.cp_destroy.restype = None
         L.cp_max_points.restype = i64
@@ -128,7 +130,8 @@ def _load():
         L.cp_status_string.restype = ctypes.c_char_p
         L.cp_last_error.restype = ctypes.c_char_p
         for fn in ("cp_plan", "cp_periodogram", "cp_best_period", "cp_sync", "cp_curve_stats",
-                   "cp_get_plan_info", "cp_bessel_coefficients", "cp_trial_frequencies"):
+                   "cp_get_plan_info", "cp_bessel_coefficients", "cp_trial_frequencies", "cp_preprocess",
+                   "cp_whiten"):
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -369,6 +372,62 @@ def cp_best_period_noalloc(times, mags, errs, offsets, grid: cp_freq_grid, sigma
     _check(_load().cp_best_period_noalloc(pt, pm, pe, off.ctypes.data, int(off.shape[0] - 1), ctypes.byref(grid),
                                           float(sigma_t), ctypes.c_void_p(stream) if stream else None, *outs),
            "cp_best_period_noalloc")
+
+
+def _device_tensor(a, name):
+    p, on_dev, keep = _ptr(a)
+    if not on_dev:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    return p, keep
+
+
+def cp_preprocess(times, mags, errs, offsets, min_n=50, stream=None):
+    """Section 5.1 cleaning on the device (see include/cp.h).  times (float64),
+    mags and errs (float32) are CUDA tensors; offsets a host int64 array.
+    Returns a dict: the kept samples ``times``, ``mags``, ``errs`` (CUDA
+    tensors), ``offsets`` over the kept curves (host), ``curve`` (input index
+    of each kept curve), ``flags`` and ``fit`` per input curve."""
+    import torch
+    pt, _ = _device_tensor(times, "times")
+    pm, _ = _device_tensor(mags, "mags")
+    pe, _ = _device_tensor(errs, "errs")
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nc = off.shape[0] - 1
+    n = int(off[-1])
+    ot = torch.empty(max(n, 1), dtype=torch.float64, device=times.device)
+    om = torch.empty(max(n, 1), dtype=torch.float32, device=times.device)
+    oe = torch.empty(max(n, 1), dtype=torch.float32, device=times.device)
+    oo = np.empty(nc + 1, np.int64)
+    flags = np.empty(nc, np.uint8)
+    fit = np.empty((nc, 3), np.float64)
+    if stream is None:
+        stream = torch.cuda.current_stream(times.device).cuda_stream
+    _check(_load().cp_preprocess(pt, pm, pe, off.ctypes.data, nc, int(min_n), ot.data_ptr(), om.data_ptr(),
+                                 oe.data_ptr(), oo.ctypes.data, flags.ctypes.data, fit.ctypes.data,
+                                 ctypes.c_void_p(stream) if stream else None), "cp_preprocess")
+    kept = np.nonzero(flags & 1)[0]
+    k = int(oo[-1])
+    return {"times": ot[:k], "mags": om[:k], "errs": oe[:k],
+            "offsets": np.concatenate([[0], np.cumsum(oo[kept + 1] - oo[kept])]).astype(np.int64),
+            "offsets_all": oo, "curve": kept, "flags": flags, "fit": fit}
+
+
+def cp_whiten(times, mags, offsets, p0, window=30, out=None, stream=None):
+    """Section 7.1 whitening on the device (see include/cp.h); returns ``out``
+    (a new CUDA float32 tensor unless given; may be ``mags`` itself)."""
+    import torch
+    pt, _ = _device_tensor(times, "times")
+    pm, _ = _device_tensor(mags, "mags")
+    if out is None:
+        out = torch.empty_like(mags)
+    po, _ = _device_tensor(out, "out")
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    p = np.ascontiguousarray(np.asarray(p0, dtype=np.float64))
+    if stream is None:
+        stream = torch.cuda.current_stream(times.device).cuda_stream
+    _check(_load().cp_whiten(pt, pm, off.ctypes.data, off.shape[0] - 1, p.ctypes.data, int(window), po,
+                             ctypes.c_void_p(stream) if stream else None), "cp_whiten")
+    return out
 
 
 def grid_from(g) -> cp_freq_grid:
