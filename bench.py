@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--dtype", default="fp16", choices=["fp16", "bf16"], help="tensor-form operand type")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-transforms", action="store_true", help="skip timing preprocessing and whitening")
     ap.add_argument("--seed", type=int, default=1)
     return ap.parse_args()
 
@@ -286,6 +287,29 @@ def main():
     value = world * n * args.steps / total_s
     plan.close()
 
+    # ---- per-curve transforms around the search (Sections 5.1 and 7.1) ----
+    transforms = None
+    if not args.no_transforms:
+        def timed_ms(fn, reps=3):
+            fn()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(e0.elapsed_time(e1))
+            return float(np.median(ts))
+        p0 = np.where(bf > 0, 1.0 / np.where(bf > 0, bf, 1.0), 0.0)
+        wout = torch.empty_like(md)
+        prep_ms = timed_ms(lambda: cp.cp_preprocess(td, md, ed, b.offsets, stream=stream.cuda_stream))
+        whiten_ms = timed_ms(lambda: cp.cp_whiten(td, md, b.offsets, p0, out=wout, stream=stream.cuda_stream))
+        transforms = {"preprocess": {"value": n / (prep_ms * 1e-3), "unit": "lightcurves/s", "ms": prep_ms,
+                                     "includes": "offsets H2D, kept-count D2H, host prefix sum (synchronous call)"},
+                      "whiten": {"value": n / (whiten_ms * 1e-3), "unit": "lightcurves/s", "ms": whiten_ms,
+                                 "p0": "best periods of the timed search"}}
+
     # ---- end to end through host buffers ---------------------------------
     e2e = None
     if not args.no_e2e:
@@ -395,6 +419,8 @@ def main():
                             "avg_launch_ms": float(info["last_tensor_kernel_ms"])}
     if tensor is not None:
         line["tensor"] = tensor
+    if transforms is not None:
+        line["transforms"] = transforms
     if getattr(g, "bands", False):
         line["bands"] = {"kernels": "k_bands + k_window", "ms_per_step": float(info["last_bands_kernel_ms"]),
                          "window_terms_per_s": info["window_terms_search"] / (info["last_bands_kernel_ms"] / 1e3),

@@ -189,3 +189,31 @@ def test_tuning_table_moves_a_class_to_the_direct_form():
     ref = oracle.batch_nckp(b, st.astype(np.float64), g.freqs())
     err = peak_err(out.cpu().numpy(), ref, range(b.n_curves))
     assert np.all(err <= TOL), err
+
+
+def test_error_matrix_on_benchmark_curves():
+    """Statistic error vs the FP64 oracle per operand type and harmonic count,
+    on six curves of the 4096-curve benchmark batch (σ_t from the skewness
+    rule) at 400 frequencies spread over its grid.  The per-curve choice
+    (n_max = 0) must meet 1e-3 in FP16; fixed counts show their truncation."""
+    b, g = synth.workload_ragged(4096, 1)
+    sub = b.subset(range(6))
+    stride = (g.n_freq - 1) // 399
+    gs = synth.Grid(g.f_min, g.df * stride, 400)
+    st = oracle.curve_stats(sub, sigma_t_mode=2)["sigma_t"].astype(np.float32)
+    ref = oracle.batch_nckp(sub, st.astype(np.float64), gs.freqs())
+    rows = range(sub.n_curves)
+    table = {}
+    for dtype, dname in ((cp.CP_DTYPE_FP16, "fp16"), (cp.CP_DTYPE_BF16, "bf16")):
+        for nm in (0, 8, 16, 32):
+            out, _, _ = run(sub, gs, sigma_t_per_curve=st, form=cp.CP_FORM_TENSOR, dtype=dtype, n_max=nm)
+            table[(dname, nm)] = float(peak_err(out, ref, rows).max())
+    out, _, _ = run(sub, gs, sigma_t_per_curve=st)
+    table[("fp32 direct", "-")] = float(peak_err(out, ref, rows).max())
+    print("\nmax peak-relative nCKP error vs the FP64 oracle (6 benchmark curves, sigma_t",
+          np.round(st, 3), "):")
+    for k, v in table.items():
+        print("  %-12s n_max %-3s %.2e" % (k[0], k[1], v))
+    assert table[("fp16", 0)] <= TOL
+    assert table[("fp32 direct", "-")] <= 1e-5
+    assert table[("bf16", 0)] <= 3e-2
