@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
                     en = pts[pn];
                     rn = rot[pn];
                     float zi, zr;
-                    sincos2pi_turns((uint32_t)((e.x + kb * e.y) >> 32), zi, zr);
+                    sincos2pi_turns_sfu((uint32_t)((e.x + kb * e.y) >> 32), zi, zr);
                     const float zr8 = fmaf(zr, r.z, -zi * r.w), zi8 = fmaf(zr, r.w, zi * r.z);
                     f2 ZR = pk(zr, zr8), ZI = pk(zi, zi8);
                     const f2 CR = pk(r.x, r.x), SR = pk(r.y, r.y), NSR = pk(-r.y, -r.y);
