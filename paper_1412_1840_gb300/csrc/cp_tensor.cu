@@ -42,6 +42,10 @@ constexpr int kTcProducers = 256;      // the last 8 warps
 // below 32 harmonics.
 __host__ __device__ constexpr int tc_ew(int nmax) { return nmax <= 16 ? 8 : 4; }
 __host__ __device__ constexpr int tc_threads(int nmax) { return 64 + 32 * tc_ew(nmax) + kTcProducers; }
+// Producer items split a frequency's harmonics into this many ranges for 32
+// harmonics (4 frequencies per unit): 64 items per stage instead of 32, so
+// three stages are produced by 192 threads instead of 96.
+__host__ __device__ constexpr int tc_hsplit(int nmax) { return nmax == 32 ? 2 : 1; }
 constexpr int kTcTablePoints = 1024;   // per-unit phase table in shared memory (producers)
 // Table slot of point j: one 16-byte pad after every 8 entries, so that the
 // eight j-octets a warp reads at once (128 bytes apart unpadded) fall on
@@ -288,7 +292,9 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     constexpr int FT = 128 / NMAX;                    // frequencies per unit (256 columns)
     constexpr int EW = tc_ew(NMAX);                   // epilogue warps
     constexpr int FH = FT / (EW / 4);                 // frequencies per epilogue warp
-    constexpr int items = 8 * FT;                     // (j-octet, frequency) per stage
+    constexpr int HS = tc_hsplit(NMAX);               // harmonic ranges per producer item
+    constexpr int NH = NMAX / HS;                     // harmonics per producer item
+    constexpr int items = 8 * FT * HS;                // (j-octet, frequency, harmonic range) per stage
     // Stages produced concurrently.  A group owns every use of its stages, so
     // it never waits more than one barrier phase ahead; hence groups <= stages.
     constexpr int groups = kTcProducers / items < kTcStages ? kTcProducers / items : kTcStages;
@@ -534,7 +540,8 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
         const int grp = pt / items;                   // stage group
         const int it = pt - grp * items;
         const int g = it & 7;                         // j-octet of the K chunk (fastest: conflict-free stores)
-        const int f = it >> 3;                        // frequency within the unit
+        const int f = (it >> 3) % FT;                 // frequency within the unit
+        const int hr = (it >> 3) / FT;                // harmonics hr*NH+1 .. (hr+1)*NH
         const bool active = grp < groups;
         uint32_t q = 0;
         bool ok = true;
@@ -577,18 +584,30 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                         pu[p] = v;
                     }
                     if (!mbar_wait(&bar_empty[s], ((q / kTcStages) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
+                    // cos/sin of harmonics n0 = hr*NH+1 and n0-1 start the Chebyshev recurrence
                     float cc[8], ss[8], c1[8], cm[8], sm[8];
 #pragma unroll
                     for (int p = 0; p < 8; p++) {
-                        float sv = 0.f, cv = 0.f;
-                        if (j0 + p < U.n) sincos2pi_turns_sfu(pu[p], sv, cv);   // Z is rounded to 16 bits
+                        float sv = 0.f, cv = 0.f, sb = 0.f, cb = 0.f, sa = 0.f, ca = 0.f;
+                        if (j0 + p < U.n) {
+                            sincos2pi_turns_sfu(pu[p], sv, cv);   // Z is rounded to 16 bits
+                            if (HS > 1 && hr > 0) {
+                                const uint32_t n0 = (uint32_t)(hr * NH + 1);
+                                sincos2pi_turns_sfu(pu[p] * n0, sb, cb);
+                                sincos2pi_turns_sfu(pu[p] * (n0 - 1u), sa, ca);
+                            } else {
+                                sb = sv; cb = cv;
+                                sa = 0.f; ca = 1.f;
+                            }
+                        }
                         c1[p] = cv;
-                        cc[p] = cv; ss[p] = sv;           // n = 1
-                        cm[p] = 1.f; sm[p] = 0.f;         // n = 0
+                        cc[p] = cb; ss[p] = sb;           // n = n0
+                        cm[p] = ca; sm[p] = sa;           // n = n0 - 1
                     }
                     unsigned char* Bs = smem + s * kTcStageBytes + 2 * kTcA;
 #pragma unroll
-                    for (int n = 1; n <= NMAX; n++) {
+                    for (int nn = 0; nn < NH; nn++) {
+                        const int n = hr * NH + 1 + nn;
                         uint32_t pc[4], ps[4];
 #pragma unroll
                         for (int p = 0; p < 8; p += 2) {
