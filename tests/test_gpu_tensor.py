@@ -217,3 +217,39 @@ def test_error_matrix_on_benchmark_curves():
     assert table[("fp16", 0)] <= TOL
     assert table[("fp32 direct", "-")] <= 1e-5
     assert table[("bf16", 0)] <= 3e-2
+
+
+def test_full_size_tensor_form_sampled():
+    """The 4096-curve, 49,981-frequency benchmark batch in the benchmark's
+    tensor-form launch configuration (device inputs, sigma_t rule, per-curve
+    harmonics, the GB300 tuning table): sampled periodogram values of six
+    curves against the oracle, and the best period is the row's argmax."""
+    import os
+    b, g = synth.workload_ragged()
+    td = torch.from_numpy(b.times).cuda(); md = torch.from_numpy(b.mags).cuda(); ed = torch.from_numpy(b.errs).cuda()
+    table = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1412_1840_gb300",
+                         "tuning_gb300.json")
+    rng = np.random.default_rng(97)
+    curves = np.sort(rng.choice(b.n_curves, 6, replace=False))
+    with cp.Plan(td, md, ed, b.offsets, cp.grid_from(g), sigma_t_mode=cp.CP_SIGMA_T_RULE,
+                 form=cp.CP_FORM_TENSOR, n_max=0, tuning=table) as p:
+        best = p.best_period()
+        out = torch.empty((b.n_curves, g.n_freq), dtype=torch.float32, device="cuda")
+        p.periodogram(out)
+        p.sync()
+        stats = p.curve_stats()
+        info = p.info()
+        rows = out[torch.from_numpy(curves).cuda()].cpu().numpy()
+    del out
+    assert sum(info["class_curves"]) == b.n_curves and info["class_curves"][2] > 3000
+    f = g.freqs()
+    for r, c in enumerate(curves):
+        assert best["best_stat"][c] == rows[r].max()
+        assert best["best_idx"][c] == int(np.argmax(rows[r]))
+        ks = np.unique(np.concatenate([rng.choice(g.n_freq, 40, replace=False),
+                                       np.clip(best["best_idx"][c] + np.arange(-6, 7), 0, g.n_freq - 1)]))
+        t, m, e = b.curve(c)
+        ref = oracle.nckp(t, m.astype(np.float64), oracle.median(e.astype(np.float64)),
+                          float(stats["sigma_t"][c]), f[ks])
+        peak = max(abs(ref).max(), abs(rows[r]).max())
+        assert np.max(np.abs(rows[r][ks] - ref)) <= TOL * peak, c
