@@ -365,9 +365,9 @@ def main():
         tensor = {
             "value": world * n * t_steps / t_total, "unit": "lightcurves/s",
             "ms_per_step": t_total * 1e3 / t_steps, "steps": t_steps,
-            "dtype": args.dtype, "n_max": "per curve (8/16/32 by truncation tail <= 1e-4)" if args.n_max == 0
+            "dtype": args.dtype, "n_max": "per curve (8/12/16/32 by truncation tail <= 1e-4)" if args.n_max == 0
             else args.n_max,
-            "class_curves": dict(zip(["direct", "n4", "n8", "n16", "n32"], ti["class_curves"])),
+            "class_curves": dict(zip(["direct", "n4", "n8", "n12", "n16", "n32"], ti["class_curves"])),
             "best_idx_agreement_vs_direct": float(np.mean(tidx == idx)),
             "best_stat_max_rel_diff_vs_direct": float(rel.max()),
             "clocks": tclk.summary(),

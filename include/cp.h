@@ -113,8 +113,8 @@ typedef struct {
  *   direct_fc[b]       frequencies per work unit of the direct form (2, 4, 8
  *                      or 16; lowered to the largest that fits the kernel's
  *                      shared trig table for the curve's N);
- *   tensor_classes[b]  with n_max = 0, bit k set lets the harmonic class
- *                      8 << k (8, 16, 32) run in the tensor form; a curve whose
+ *   tensor_classes[b]  with n_max = 0, bit 0, 1, 2, 3 set lets the harmonic
+ *                      class 8, 16, 32, 12 run in the tensor form; a curve whose
  *                      class bit is clear runs in the direct form.
  * Curves above the last bucket, and plans without tuning, use the built-in
  * choices (16 frequencies per unit where they fit; every class in the tensor
@@ -135,8 +135,8 @@ typedef struct {
     float alpha;                     /* error-bar correction factor of Eq. (pSNR), >0   */
     int32_t form;                    /* CP_FORM_*                                       */
     int32_t dtype;                   /* CP_DTYPE_* (tensor form only)                   */
-    int32_t n_max;                   /* harmonics of the tensor form (4, 8, 16, 32); 0 = */
-                                     /* per curve: the smallest of 8, 16, 32 whose      */
+    int32_t n_max;                   /* harmonics of the tensor form (4, 8, 12, 16, 32); */
+                                     /* 0 = per curve: the smallest of 8, 12, 16, 32 whose */
                                      /* truncation tail is <= 1e-4 of the kernel peak   */
                                      /* for the curve's sigma_t at plan time; curves    */
                                      /* that need more run in the direct form           */
@@ -276,8 +276,8 @@ typedef struct {
     float last_step_ms;           /* device time of the whole last cp_best_period       */
     int32_t n_sm;                 /* SMs of the plan's device                           */
     int32_t max_n;                /* largest N in the batch                             */
-    int64_t class_curves[5];      /* curves per evaluation class: direct form, then the */
-                                  /* tensor form with 4, 8, 16, 32 harmonics            */
+    int64_t class_curves[6];      /* curves per evaluation class: direct form, then the */
+                                  /* tensor form with 4, 8, 12, 16, 32 harmonics        */
     float last_tensor_kernel_ms;  /* device time of the tensor-form launches, last call */
     float last_direct_kernel_ms;  /* device time of the direct-form launches, last call */
     double tensor_flops_search;   /* tensor-form GEMM flops of one cp_best_period:      */

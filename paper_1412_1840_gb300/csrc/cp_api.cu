@@ -106,7 +106,7 @@ struct cp_plan_s {
     std::vector<int32_t> order;          // slot -> curve
     std::vector<int32_t> fc;             // per curve
     std::vector<int32_t> cls;            // per curve: 0 direct, else tensor harmonics
-    int64_t class_count[5] = {0, 0, 0, 0, 0};   // curves per class {direct, 4, 8, 16, 32}
+    int64_t class_count[6] = {0, 0, 0, 0, 0, 0};   // curves per class {direct, 4, 8, 12, 16, 32}
     std::vector<int64_t> unit_full, unit_coarse, unit_fine, unit_list, wtile;
     std::vector<Wave> waves;
     size_t pair_smem = 0;
@@ -187,8 +187,9 @@ int class_rank(int cls)
     switch (cls) {
     case 4: return 1;
     case 8: return 2;
-    case 16: return 3;
-    case 32: return 4;
+    case 12: return 3;
+    case 16: return 4;
+    case 32: return 5;
     }
     return 0;   // direct form
 }
@@ -204,15 +205,15 @@ double harmonic_tail(double sigma_t, int n)
     return 1.0 - s;
 }
 
-// Smallest harmonic count of the tensor form whose truncation tail stays
-// below 1e-4 of the kernel peak; 0 (direct form) when even 32 harmonics do
+// Smallest harmonic count of the tensor form (8, 12, 16, 32) whose truncation
+// tail stays below 1e-4 of the kernel peak; 0 (direct form) when even 32 harmonics do
 // not reach it (sigma_t below about 0.13).  The tail falls as sigma_t grows,
 // so each class is a threshold on sigma_t, found once by bisection.
 int harmonics_for(float sigma_t)
 {
     static const std::vector<double> thr = [] {
         std::vector<double> t;
-        for (int n : {8, 16, 32}) {
+        for (int n : {8, 12, 16, 32}) {
             double lo = 0.02, hi = 4.0;
             for (int it = 0; it < 40; it++) {
                 const double mid = 0.5 * (lo + hi);
@@ -222,8 +223,8 @@ int harmonics_for(float sigma_t)
         }
         return t;
     }();
-    const int cls[3] = {8, 16, 32};
-    for (int k = 0; k < 3; k++)
+    const int cls[4] = {8, 12, 16, 32};
+    for (int k = 0; k < 4; k++)
         if ((double)sigma_t >= thr[k]) return cls[k];
     return 0;
 }
@@ -706,8 +707,9 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     if (opt.form == CP_FORM_TENSOR) {
         if (opt.dtype != CP_DTYPE_FP16 && opt.dtype != CP_DTYPE_BF16)
             return fail(CP_EINVAL, "cp_plan: dtype must be CP_DTYPE_FP16 or CP_DTYPE_BF16");
-        if (opt.n_max != 0 && opt.n_max != 4 && opt.n_max != 8 && opt.n_max != 16 && opt.n_max != 32)
-            return fail(CP_EINVAL, "cp_plan: n_max must be 0 (per curve), 4, 8, 16 or 32");
+        if (opt.n_max != 0 && opt.n_max != 4 && opt.n_max != 8 && opt.n_max != 12 && opt.n_max != 16 &&
+            opt.n_max != 32)
+            return fail(CP_EINVAL, "cp_plan: n_max must be 0 (per curve), 4, 8, 12, 16 or 32");
         p->tensor = true;
         p->n_max = opt.n_max;
         // test hook: shorter bounded waits, to exercise the timeout path
@@ -734,8 +736,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
                 return fail(CP_EINVAL, "cp_plan: tuning.bucket_max_n must be >= 2 and strictly ascending");
             if (fc != 2 && fc != 4 && fc != 8 && fc != 16)
                 return fail(CP_EINVAL, "cp_plan: tuning.direct_fc must be 2, 4, 8 or 16");
-            if (tune.tensor_classes[b] < 0 || tune.tensor_classes[b] > 7)
-                return fail(CP_EINVAL, "cp_plan: tuning.tensor_classes must be a 3-bit mask");
+            if (tune.tensor_classes[b] < 0 || tune.tensor_classes[b] > 15)
+                return fail(CP_EINVAL, "cp_plan: tuning.tensor_classes must be a 4-bit mask");
         }
         opt.tuning = nullptr;   // copied; the caller's struct is not kept
     }
@@ -854,7 +856,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             for (int64_t c = 0; c < n_curves; c++) {
                 int cl = harmonics_for(st[c]);
                 const int tb = tune_bucket(tune, (int)(offsets[c + 1] - offsets[c]));
-                const int bit = cl == 8 ? 1 : cl == 16 ? 2 : cl == 32 ? 4 : 0;
+                const int bit = cl == 8 ? 1 : cl == 16 ? 2 : cl == 32 ? 4 : cl == 12 ? 8 : 0;
                 if (tb >= 0 && bit && !(tune.tensor_classes[tb] & bit)) cl = 0;   // tuned: direct form is faster here
                 p->cls[c] = cl;
             }
@@ -1049,7 +1051,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             return fail(CP_EUNSUPPORTED, "cp_plan: spectral-window buffers do not fit in shared memory");
         CP_CUDA(prepare_bands_kernels(p->np2max, p->max_band_points, g.trials_per_band));
     }
-    for (int nm : {4, 8, 16, 32})
+    for (int nm : {4, 8, 12, 16, 32})
         if (p->class_count[class_rank(nm)]) CP_CUDA(prepare_tensor_kernel(nm));   // one CTA per SM
     {
         int occ = 1;
@@ -1239,7 +1241,7 @@ cp_status cp_get_plan_info(cp_plan_t p, cp_plan_info* info)
     info->last_step_ms = p->last_step_ms;
     info->n_sm = p->n_sm;
     info->max_n = p->max_n;
-    for (int k = 0; k < 5; k++) info->class_curves[k] = p->class_count[k];
+    for (int k = 0; k < 6; k++) info->class_curves[k] = p->class_count[k];
     info->last_tensor_kernel_ms = p->last_tensor_ms;
     info->last_direct_kernel_ms = p->last_direct_ms;
     info->tensor_flops_search = p->tensor_flops;

@@ -37,10 +37,11 @@ constexpr int kTcCols = 256;           // columns per unit
 constexpr int kTcProducers = 256;      // the last 8 warps
 // Epilogue warps: 8 for up to 16 harmonics (two warps per TMEM lane group,
 // each taking half of the unit's frequencies), else 4; the drain of an
-// accumulator is on the MMA's critical path.  With 18 warps a quarter-SM
+// accumulator is on the MMA's critical path (a warp's share must be an even
+// number of frequencies: 12 harmonics keep 4 warps).  With 18 warps a quarter-SM
 // holds up to 5 of them, which caps registers at 96 per thread: enough
 // below 32 harmonics.
-__host__ __device__ constexpr int tc_ew(int nmax) { return nmax <= 16 ? 8 : 4; }
+__host__ __device__ constexpr int tc_ew(int nmax) { return nmax <= 16 && (128 / nmax / 2) % 2 == 0 ? 8 : 4; }
 __host__ __device__ constexpr int tc_threads(int nmax) { return 64 + 32 * tc_ew(nmax) + kTcProducers; }
 // Producer items split a frequency's harmonics into this many ranges for 32
 // harmonics (4 frequencies per unit): 64 items per stage instead of 32, so
@@ -289,9 +290,11 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     __shared__ float s_red[8][32];
     __shared__ float s_acc[32];
 
-    constexpr int FT = 128 / NMAX;                    // frequencies per unit (256 columns)
+    constexpr int FT = 128 / NMAX;                    // frequencies per unit
+    constexpr int COLS = FT * 2 * NMAX;               // columns of the unit: 256, or 240 for 12 harmonics
     constexpr int EW = tc_ew(NMAX);                   // epilogue warps
     constexpr int FH = FT / (EW / 4);                 // frequencies per epilogue warp
+    constexpr int FHP = FH <= 2 ? 2 : FH <= 4 ? 4 : FH <= 8 ? 8 : FH <= 16 ? 16 : 32;   // padded to a power of 2
     constexpr int HS = tc_hsplit(NMAX);               // harmonic ranges per producer item
     constexpr int NH = NMAX / HS;                     // harmonics per producer item
     constexpr int items = 8 * FT * HS;                // (j-octet, frequency, harmonic range) per stage
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_f16(128, kTcCols, BF);
+            constexpr uint32_t idesc = idesc_f16(128, COLS, BF);
             uint32_t q = 0, m = 0;
             bool ok = true;
             for (int64_t u = a.unit_begin + blockIdx.x / a.ctas_per_unit; ok && u < a.unit_end; u += gridDim.x) {
@@ -446,7 +449,9 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                     const uint64_t ph0_h = h ? ph0[1] : ph0[0];
                     const uint64_t pstep_h = h ? pstep[1] : pstep[0];
                     const bool has = 2 * P + h < U.nmt;
-                    float accf[FH];
+                    float accf[FHP];
+#pragma unroll
+                    for (int fi = FH; fi < FHP; fi++) accf[fi] = 0.f;
                     if (has) {
                         const uint32_t tbase = taddr + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * kTcCols) + hcol;
                         float v[32];
@@ -484,8 +489,8 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                     mbar_arrive(&bar_tempty[h]);
                     if (has) {
                         // sum over the 128 rows, fixed order
-                        const float x = warp_reduce_scatter<FH>(accf, lane);
-                        constexpr int SH = FH == 2 ? 4 : FH == 4 ? 3 : FH == 8 ? 2 : FH == 16 ? 1 : 0;
+                        const float x = warp_reduce_scatter<FHP>(accf, lane);
+                        constexpr int SH = FHP == 2 ? 4 : FHP == 4 ? 3 : FHP == 8 ? 2 : FHP == 16 ? 1 : 0;
                         if ((lane & ((1 << SH) - 1)) == 0) s_red[ew][lane >> SH] = x;
                         asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
                         if (ew == 0 && lane < FT) {
@@ -661,6 +666,7 @@ cudaError_t prepare_tensor_kernel(int n_max)
     switch (n_max) {
     case 4: e = set_tensor_smem<4, false>(); if (e == cudaSuccess) e = set_tensor_smem<4, true>(); break;
     case 8: e = set_tensor_smem<8, false>(); if (e == cudaSuccess) e = set_tensor_smem<8, true>(); break;
+    case 12: e = set_tensor_smem<12, false>(); if (e == cudaSuccess) e = set_tensor_smem<12, true>(); break;
     case 16: e = set_tensor_smem<16, false>(); if (e == cudaSuccess) e = set_tensor_smem<16, true>(); break;
     case 32: e = set_tensor_smem<32, false>(); if (e == cudaSuccess) e = set_tensor_smem<32, true>(); break;
     }
@@ -698,6 +704,7 @@ cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s)
     switch (a.n_max) {
         CP_TC_LAUNCH(4)
         CP_TC_LAUNCH(8)
+        CP_TC_LAUNCH(12)
         CP_TC_LAUNCH(16)
         CP_TC_LAUNCH(32)
     default: return cudaErrorInvalidValue;

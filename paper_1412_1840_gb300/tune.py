@@ -1,7 +1,7 @@
 """Autotuner of the launch choices the plan makes per curve size:
 
 * frequencies per work unit of the direct form (2, 4, 8 or 16), and
-* for each harmonic class of the tensor form (8, 16, 32 harmonics) whether
+* for each harmonic class of the tensor form (8, 12, 16, 32 harmonics) whether
   the tensor form or the direct form is faster at that curve size (the
   tensor form pads a curve to 128-row tiles, which costs most for small N).
 
@@ -81,7 +81,7 @@ def tune(n_freq: int = 2048, target_pair_freq: float = 4e10, seed: int = 0, devi
             if r["pair_freq_per_s"] > best_rate:
                 best_fc, best_rate = fc, r["pair_freq_per_s"]
         entry["direct_fc"] = best_fc
-        for cls in (8, 16, 32):
+        for cls in (8, 12, 16, 32):
             r = timed(t, y, e, off, grid, form=CP_FORM_TENSOR, n_max=cls, device=device)
             entry["tensor_rate"][str(cls)] = r["pair_freq_per_s"]
             entry["tensor"][str(cls)] = bool(r["pair_freq_per_s"] > best_rate)

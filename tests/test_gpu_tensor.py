@@ -57,7 +57,7 @@ def ragged():
     return b, g, ref
 
 
-@pytest.mark.parametrize("n_max", [16, 32])
+@pytest.mark.parametrize("n_max", [12, 16, 32])
 def test_tensor_fp16_parity_ragged(ragged, n_max):
     b, g, ref = ragged
     out, best, _ = run(b, g, sigma_t=0.45, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_FP16, n_max=n_max)
@@ -148,7 +148,7 @@ def test_bounded_waits_report_timeout_and_keep_context():
 
 
 def test_tensor_auto_harmonics_per_curve():
-    """n_max = 0 picks per curve the smallest of 8/16/32 harmonics whose
+    """n_max = 0 picks per curve the smallest of 8/12/16/32 harmonics whose
     truncation tail is <= 1e-4; curves with sigma_t too small for 32 run in the
     direct form.  Every curve must meet the tensor tolerance."""
     b = synth.ragged_batch(10, seed=33, n_lo=150, n_hi=600)
@@ -162,7 +162,7 @@ def test_tensor_auto_harmonics_per_curve():
         best = p.best_period()
         info = p.info()
     out = out.cpu().numpy()
-    assert info["class_curves"] == [2, 0, 2, 3, 3]       # direct, 4, 8, 16, 32 harmonics
+    assert info["class_curves"] == [2, 0, 2, 1, 2, 3]    # direct, 4, 8, 12, 16, 32 harmonics
     ref = oracle.batch_nckp(b, st.astype(np.float64), g.freqs())
     err = peak_err(out, ref, range(b.n_curves))
     assert np.all(err <= TOL), err
@@ -185,7 +185,7 @@ def test_tuning_table_moves_a_class_to_the_direct_form():
         info = p.info()
     small = int(np.sum(b.sizes <= 400))
     assert 0 < small < b.n_curves
-    assert info["class_curves"] == [small, 0, 0, b.n_curves - small, 0]
+    assert info["class_curves"] == [small, 0, 0, 0, b.n_curves - small, 0]
     ref = oracle.batch_nckp(b, st.astype(np.float64), g.freqs())
     err = peak_err(out.cpu().numpy(), ref, range(b.n_curves))
     assert np.all(err <= TOL), err
@@ -205,7 +205,7 @@ def test_error_matrix_on_benchmark_curves():
     rows = range(sub.n_curves)
     table = {}
     for dtype, dname in ((cp.CP_DTYPE_FP16, "fp16"), (cp.CP_DTYPE_BF16, "bf16")):
-        for nm in (0, 8, 16, 32):
+        for nm in (0, 8, 12, 16, 32):
             out, _, _ = run(sub, gs, sigma_t_per_curve=st, form=cp.CP_FORM_TENSOR, dtype=dtype, n_max=nm)
             table[(dname, nm)] = float(peak_err(out, ref, rows).max())
     out, _, _ = run(sub, gs, sigma_t_per_curve=st)
