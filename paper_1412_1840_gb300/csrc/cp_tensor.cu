@@ -11,12 +11,21 @@
 // 256 columns = frequencies x harmonics x {cos, sin}) is a chain of GEMMs
 // D_I = W'[I, J >= I] * Z[J, cols] on tcgen05 (M = 128, N = 256, K = 64 per
 // stage, FP16 or BF16 operands, FP32 accumulation in TMEM), followed by the
-// epilogue q = sum_i Z[i, col] D_I[i, col] weighted by a_n.
+// epilogue q = sum_i z[i, col] D_I[i, col].  Up to 16 harmonics the weights
+// a_n are folded into the GEMM operand (column n of Z holds a_n z_n), so the
+// epilogue multiplies by the unweighted z_n; with 32 harmonics the producers'
+// registers are the tighter resource and the epilogue applies a_n.
 //
-// Warp roles (14 warps): warp 0 bulk-copies pre-swizzled W' tiles, warp 1
-// issues the MMAs, warps 2-5 read TMEM (epilogue), warps 6-13 generate the Z
+// Warp roles: warp 0 bulk-copies pre-swizzled W' tiles, warp 1 issues the
+// MMAs, the next 4 or 8 warps read TMEM (epilogue), the last 8 generate the Z
 // tiles (cos/sin of every harmonic by the Chebyshev recurrence) straight into
 // the swizzled shared-memory layout the MMA reads.  Every wait is bounded.
+//
+// With folded weights both sides run the recurrence on x_n = sigma_n (cos n th,
+// sin n th) with the sign pattern sigma = +, +, -, -, ... (period 4 in n,
+// n = 0, 1, 2, ...).  Then x_{n+1} = K_n x_n + x_{n-1} with K_n = +2 cos th for
+// even n and -2 cos th for odd n: one packed f32x2 FMA per step and no
+// negation.  The signs cancel in the product z_n (W' z_n).
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -298,6 +307,9 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     constexpr int HS = tc_hsplit(NMAX);               // harmonic ranges per producer item
     constexpr int NH = NMAX / HS;                     // harmonics per producer item
     constexpr int items = 8 * FT * HS;                // (j-octet, frequency, harmonic range) per stage
+    constexpr bool FOLD = NMAX <= 16;                 // a_n folded into Z (see the file header)
+    // a producer's harmonic range starts at n0 = hr NH + 1 with sigma_{n0-1} = sigma_{n0} = +
+    static_assert(!FOLD || HS == 1 || NH % 4 == 0, "harmonic ranges must start on the sign pattern's period");
     // Stages produced concurrently.  A group owns every use of its stages, so
     // it never waits more than one barrier phase ahead; hence groups <= stages.
     constexpr int groups = kTcProducers / items < kTcStages ? kTcProducers / items : kTcStages;
@@ -419,9 +431,11 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
             if (U.empty) continue;
             const CurveParams& P_ = a.cp[U.c];
             const int64_t off = P_.off;
-            float an[NMAX];
+            float an[FOLD ? 1 : NMAX];
+            if constexpr (!FOLD) {
 #pragma unroll
-            for (int q = 0; q < NMAX; q++) an[q] = a.coef[(int64_t)U.c * a.coef_stride + q];
+                for (int q = 0; q < NMAX; q++) an[q] = a.coef[(int64_t)U.c * a.coef_stride + q];
+            }
             for (int P = 0; 2 * P < U.nmt; P++, m++) {
                 // the rows' phases for both M-tiles, loaded before the wait
                 uint64_t ph0[2] = {0, 0}, pstep[2] = {0, 0};
@@ -470,18 +484,38 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                                     s1 = sn;
                                 }
                             }
-                            float cp2 = 1.f, sp2 = 0.f, cp1 = c1, sp1 = s1;
-                            float acc = 0.f;
+                            if constexpr (FOLD) {
+                                // x_{n-1}, x_n (signed as the producers sign them)
+                                f2 xp = pk(1.f, 0.f), xc = pk(c1, s1), acc2 = 0ull;
+                                const f2 kp = pk(2.f * c1, 2.f * c1), km = pk(-2.f * c1, -2.f * c1);
 #pragma unroll
-                            for (int n = 1; n <= NMAX; n++) {
-                                const int col = fi * 2 * NMAX + 2 * (n - 1);   // relative to hcol
-                                if ((col & 31) == 0) tmem_ld32(tbase + col, v);
-                                acc = fmaf(an[n - 1], fmaf(v[col & 31], cp1, v[(col & 31) + 1] * sp1), acc);
-                                const float cn = fmaf(2.f * c1, cp1, -cp2), sn = fmaf(2.f * c1, sp1, -sp2);
-                                cp2 = cp1; sp2 = sp1;
-                                cp1 = cn; sp1 = sn;
+                                for (int n = 1; n <= NMAX; n++) {
+                                    const int col = fi * 2 * NMAX + 2 * (n - 1);   // relative to hcol
+                                    if ((col & 31) == 0) tmem_ld32(tbase + col, v);
+                                    acc2 = fma2(pk(v[col & 31], v[(col & 31) + 1]), xc, acc2);
+                                    if (n < NMAX) {
+                                        const f2 xn = fma2((n & 1) ? km : kp, xc, xp);
+                                        xp = xc;
+                                        xc = xn;
+                                    }
+                                }
+                                float acc_c, acc_s;
+                                upk(acc2, acc_c, acc_s);
+                                accf[fi] = live_h ? acc_c + acc_s : 0.f;
+                            } else {
+                                float cp2 = 1.f, sp2 = 0.f, cp1 = c1, sp1 = s1;
+                                float acc = 0.f;
+#pragma unroll
+                                for (int n = 1; n <= NMAX; n++) {
+                                    const int col = fi * 2 * NMAX + 2 * (n - 1);   // relative to hcol
+                                    if ((col & 31) == 0) tmem_ld32(tbase + col, v);
+                                    acc = fmaf(an[n - 1], fmaf(v[col & 31], cp1, v[(col & 31) + 1] * sp1), acc);
+                                    const float cn = fmaf(2.f * c1, cp1, -cp2), sn = fmaf(2.f * c1, sp1, -sp2);
+                                    cp2 = cp1; sp2 = sp1;
+                                    cp1 = cn; sp1 = sn;
+                                }
+                                accf[fi] = live_h ? acc : 0.f;
                             }
-                            accf[fi] = live_h ? acc : 0.f;
                         }
                     }
                     // release this accumulator (always, so the phases of both buffers advance per pair)
@@ -558,6 +592,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
             const int64_t off = a.cp[U.c].off;
             const bool tab = U.n <= kTcTablePoints;
             const uint64_t mf = tc_mult<LIST>(a, U, f);   // this producer's frequency multiplier
+            const float* anp = a.coef + (int64_t)U.c * a.coef_stride + hr * NH;   // a_n of this harmonic range
             if (tab) {
                 // every producer is done with the previous unit's table
                 asm volatile("bar.sync 2, 256;" ::: "memory");
@@ -589,45 +624,104 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                         pu[p] = v;
                     }
                     if (!mbar_wait(&bar_empty[s], ((q / kTcStages) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
-                    // cos/sin of harmonics n0 = hr*NH+1 and n0-1 start the Chebyshev recurrence
-                    float cc[8], ss[8], c1[8], cm[8], sm[8];
+                    if constexpr (FOLD) {
+                        // x_{n0} and x_{n0-1} (n0 = hr*NH+1, both signed +) start the recurrence;
+                        // f32x2 lanes are the points 2r and 2r+1
+                        f2 cc[4], ss[4], cm[4], sm[4], kp[4], km[4];
 #pragma unroll
-                    for (int p = 0; p < 8; p++) {
-                        float sv = 0.f, cv = 0.f, sb = 0.f, cb = 0.f, sa = 0.f, ca = 0.f;
-                        if (j0 + p < U.n) {
-                            sincos2pi_turns_sfu(pu[p], sv, cv);   // Z is rounded to 16 bits
-                            if (HS > 1 && hr > 0) {
-                                const uint32_t n0 = (uint32_t)(hr * NH + 1);
-                                sincos2pi_turns_sfu(pu[p] * n0, sb, cb);
-                                sincos2pi_turns_sfu(pu[p] * (n0 - 1u), sa, ca);
-                            } else {
-                                sb = sv; cb = cv;
-                                sa = 0.f; ca = 1.f;
+                        for (int r = 0; r < 4; r++) {
+                            float sv[2], cv[2], sb[2], cb[2], sa[2], ca[2];
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                const int p = 2 * r + h;
+                                sv[h] = 0.f; cv[h] = 0.f; sb[h] = 0.f; cb[h] = 0.f; sa[h] = 0.f; ca[h] = 0.f;
+                                if (j0 + p < U.n) {
+                                    sincos2pi_turns_sfu(pu[p], sv[h], cv[h]);   // Z is rounded to 16 bits
+                                    if (HS > 1 && hr > 0) {
+                                        const uint32_t n0 = (uint32_t)(hr * NH + 1);
+                                        sincos2pi_turns_sfu(pu[p] * n0, sb[h], cb[h]);
+                                        sincos2pi_turns_sfu(pu[p] * (n0 - 1u), sa[h], ca[h]);
+                                    } else {
+                                        sb[h] = sv[h]; cb[h] = cv[h];
+                                        sa[h] = 0.f; ca[h] = 1.f;
+                                    }
+                                }
+                            }
+                            kp[r] = pk(2.f * cv[0], 2.f * cv[1]);
+                            km[r] = pk(-2.f * cv[0], -2.f * cv[1]);
+                            cc[r] = pk(cb[0], cb[1]); ss[r] = pk(sb[0], sb[1]);     // n = n0
+                            cm[r] = pk(ca[0], ca[1]); sm[r] = pk(sa[0], sa[1]);     // n = n0 - 1
+                        }
+                        unsigned char* Bs = smem + s * kTcStageBytes + 2 * kTcA;
+#pragma unroll
+                        for (int nn = 0; nn < NH; nn++) {
+                            const int n = hr * NH + 1 + nn;
+                            const float an = __ldg(anp + nn);
+                            const f2 a2 = pk(an, an);
+                            uint32_t pc[4], ps[4];
+#pragma unroll
+                            for (int r = 0; r < 4; r++) {
+                                float lo, hi;
+                                upk(mul2(a2, cc[r]), lo, hi);
+                                pc[r] = pack16x2<BF>(lo, hi);
+                                upk(mul2(a2, ss[r]), lo, hi);
+                                ps[r] = pack16x2<BF>(lo, hi);
+                            }
+                            const int col = f * 2 * NMAX + 2 * (n - 1);
+                            *reinterpret_cast<uint4*>(Bs + sw128_offset(col, g * 8)) = make_uint4(pc[0], pc[1], pc[2], pc[3]);
+                            *reinterpret_cast<uint4*>(Bs + sw128_offset(col + 1, g * 8)) = make_uint4(ps[0], ps[1], ps[2], ps[3]);
+                            if (nn + 1 < NH) {
+#pragma unroll
+                                for (int r = 0; r < 4; r++) {
+                                    const f2 k = (n & 1) ? km[r] : kp[r];
+                                    const f2 cn = fma2(k, cc[r], cm[r]);
+                                    const f2 sn = fma2(k, ss[r], sm[r]);
+                                    cm[r] = cc[r]; sm[r] = ss[r];
+                                    cc[r] = cn; ss[r] = sn;
+                                }
                             }
                         }
-                        c1[p] = cv;
-                        cc[p] = cb; ss[p] = sb;           // n = n0
-                        cm[p] = ca; sm[p] = sa;           // n = n0 - 1
-                    }
-                    unsigned char* Bs = smem + s * kTcStageBytes + 2 * kTcA;
-#pragma unroll
-                    for (int nn = 0; nn < NH; nn++) {
-                        const int n = hr * NH + 1 + nn;
-                        uint32_t pc[4], ps[4];
-#pragma unroll
-                        for (int p = 0; p < 8; p += 2) {
-                            pc[p >> 1] = pack16x2<BF>(cc[p], cc[p + 1]);
-                            ps[p >> 1] = pack16x2<BF>(ss[p], ss[p + 1]);
-                        }
-                        const int col = f * 2 * NMAX + 2 * (n - 1);
-                        *reinterpret_cast<uint4*>(Bs + sw128_offset(col, g * 8)) = make_uint4(pc[0], pc[1], pc[2], pc[3]);
-                        *reinterpret_cast<uint4*>(Bs + sw128_offset(col + 1, g * 8)) = make_uint4(ps[0], ps[1], ps[2], ps[3]);
+                    } else {
+                        // cos/sin of harmonics n0 = hr*NH+1 and n0-1 start the Chebyshev recurrence
+                        float cc[8], ss[8], c1[8], cm[8], sm[8];
 #pragma unroll
                         for (int p = 0; p < 8; p++) {
-                            const float cn = fmaf(2.f * c1[p], cc[p], -cm[p]);
-                            const float sn = fmaf(2.f * c1[p], ss[p], -sm[p]);
-                            cm[p] = cc[p]; sm[p] = ss[p];
-                            cc[p] = cn; ss[p] = sn;
+                            float sv = 0.f, cv = 0.f, sb = 0.f, cb = 0.f, sa = 0.f, ca = 0.f;
+                            if (j0 + p < U.n) {
+                                sincos2pi_turns_sfu(pu[p], sv, cv);   // Z is rounded to 16 bits
+                                if (HS > 1 && hr > 0) {
+                                    const uint32_t n0 = (uint32_t)(hr * NH + 1);
+                                    sincos2pi_turns_sfu(pu[p] * n0, sb, cb);
+                                    sincos2pi_turns_sfu(pu[p] * (n0 - 1u), sa, ca);
+                                } else {
+                                    sb = sv; cb = cv;
+                                    sa = 0.f; ca = 1.f;
+                                }
+                            }
+                            c1[p] = cv;
+                            cc[p] = cb; ss[p] = sb;           // n = n0
+                            cm[p] = ca; sm[p] = sa;           // n = n0 - 1
+                        }
+                        unsigned char* Bs = smem + s * kTcStageBytes + 2 * kTcA;
+#pragma unroll
+                        for (int nn = 0; nn < NH; nn++) {
+                            const int n = hr * NH + 1 + nn;
+                            uint32_t pc[4], ps[4];
+#pragma unroll
+                            for (int p = 0; p < 8; p += 2) {
+                                pc[p >> 1] = pack16x2<BF>(cc[p], cc[p + 1]);
+                                ps[p >> 1] = pack16x2<BF>(ss[p], ss[p + 1]);
+                            }
+                            const int col = f * 2 * NMAX + 2 * (n - 1);
+                            *reinterpret_cast<uint4*>(Bs + sw128_offset(col, g * 8)) = make_uint4(pc[0], pc[1], pc[2], pc[3]);
+                            *reinterpret_cast<uint4*>(Bs + sw128_offset(col + 1, g * 8)) = make_uint4(ps[0], ps[1], ps[2], ps[3]);
+#pragma unroll
+                            for (int p = 0; p < 8; p++) {
+                                const float cn = fmaf(2.f * c1[p], cc[p], -cm[p]);
+                                const float sn = fmaf(2.f * c1[p], ss[p], -sm[p]);
+                                cm[p] = cc[p]; sm[p] = ss[p];
+                                cc[p] = cn; ss[p] = sn;
+                            }
                         }
                     }
                     fence_proxy_async_smem();
