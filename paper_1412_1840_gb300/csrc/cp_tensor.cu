@@ -43,7 +43,6 @@ constexpr int kTcA = 16384;            // 128 x 64 x 2 B
 constexpr int kTcB = 32768;            // 256 x 64 x 2 B
 constexpr int kTcStageBytes = 2 * kTcA + kTcB;   // W' tiles of two M-tiles + one Z tile
 constexpr int kTcCols = 256;           // columns per unit
-constexpr int kTcProducers = 256;      // the last 8 warps
 // Epilogue warps: 8 for up to 16 harmonics (two warps per TMEM lane group,
 // each taking half of the unit's frequencies), else 4; the drain of an
 // accumulator is on the MMA's critical path (a warp's share must be an even
@@ -51,11 +50,19 @@ constexpr int kTcProducers = 256;      // the last 8 warps
 // holds up to 5 of them, which caps registers at 96 per thread: enough
 // below 32 harmonics.
 __host__ __device__ constexpr int tc_ew(int nmax) { return nmax <= 16 && (128 / nmax / 2) % 2 == 0 ? 8 : 4; }
-__host__ __device__ constexpr int tc_threads(int nmax) { return 64 + 32 * tc_ew(nmax) + kTcProducers; }
 // Producer items split a frequency's harmonics into this many ranges for 32
 // harmonics (4 frequencies per unit): 64 items per stage instead of 32, so
 // three stages are produced by 192 threads instead of 96.
 __host__ __device__ constexpr int tc_hsplit(int nmax) { return nmax == 32 ? 2 : 1; }
+// Items of one Z stage: (j-octet, frequency, harmonic range).  A stage group
+// takes a whole number of warps: a warp split between two groups would run
+// both groups' work one after the other.
+__host__ __device__ constexpr int tc_items(int nmax) { return 8 * (128 / nmax) * tc_hsplit(nmax); }
+__host__ __device__ constexpr int tc_gstride(int nmax) { return (tc_items(nmax) + 31) / 32 * 32; }
+// Producer threads: 8 warps; 9 for 12 harmonics, so that three 80-item groups
+// (padded to 96 threads) produce three stages at once.
+__host__ __device__ constexpr int tc_producers(int nmax) { return nmax == 12 ? 288 : 256; }
+__host__ __device__ constexpr int tc_threads(int nmax) { return 64 + 32 * tc_ew(nmax) + tc_producers(nmax); }
 constexpr int kTcTablePoints = 1024;   // per-unit phase table in shared memory (producers)
 // Table slot of point j: one 16-byte pad after every 8 entries, so that the
 // eight j-octets a warp reads at once (128 bytes apart unpadded) fall on
@@ -297,7 +304,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     __shared__ uint32_t s_taddr;
     __shared__ int s_abort;
     __shared__ float s_red[8][32];
-    __shared__ float s_acc[32];
+    __shared__ float s_acc[32];                       // per-accumulator reduction: running sums
 
     constexpr int FT = 128 / NMAX;                    // frequencies per unit
     constexpr int COLS = FT * 2 * NMAX;               // columns of the unit: 256, or 240 for 12 harmonics
@@ -306,13 +313,20 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     constexpr int FHP = FH <= 2 ? 2 : FH <= 4 ? 4 : FH <= 8 ? 8 : FH <= 16 ? 16 : 32;   // padded to a power of 2
     constexpr int HS = tc_hsplit(NMAX);               // harmonic ranges per producer item
     constexpr int NH = NMAX / HS;                     // harmonics per producer item
-    constexpr int items = 8 * FT * HS;                // (j-octet, frequency, harmonic range) per stage
+    constexpr int items = tc_items(NMAX);             // (j-octet, frequency, harmonic range) per stage
+    constexpr int PROD = tc_producers(NMAX);
+    constexpr int GS = tc_gstride(NMAX);              // threads per stage group
     constexpr bool FOLD = NMAX <= 16;                 // a_n folded into Z (see the file header)
+    // Row sums reduced across the warp once per unit (per-thread partial sums over
+    // the M-tiles) or once per accumulator; the latter measured faster only for
+    // 16 harmonics, where the former raises register spills.
+    constexpr bool UNIT_RED = NMAX != 16;
     // a producer's harmonic range starts at n0 = hr NH + 1 with sigma_{n0-1} = sigma_{n0} = +
     static_assert(!FOLD || HS == 1 || NH % 4 == 0, "harmonic ranges must start on the sign pattern's period");
+    static_assert(!FOLD || NH % 2 == 0, "the producers take the step's sign from the parity of nn");
     // Stages produced concurrently.  A group owns every use of its stages, so
     // it never waits more than one barrier phase ahead; hence groups <= stages.
-    constexpr int groups = kTcProducers / items < kTcStages ? kTcProducers / items : kTcStages;
+    constexpr int groups = PROD / GS < kTcStages ? PROD / GS : kTcStages;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
@@ -424,6 +438,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
         const int fh = ew >> 2;                       // which FH frequencies of the unit
         const uint32_t hcol = (uint32_t)(fh * FH * 2 * NMAX);   // their first column (a multiple of 32)
         constexpr bool list = LIST;                   // explicit frequencies: no rotation shortcut
+        constexpr int SH = FHP == 2 ? 4 : FHP == 4 ? 3 : FHP == 8 ? 2 : FHP == 16 ? 1 : 0;   // lanes per sum
         uint32_t m = 0;
         bool ok = true;
         for (int64_t u = a.unit_begin + blockIdx.x / a.ctas_per_unit; ok && u < a.unit_end; u += gridDim.x) {
@@ -436,6 +451,11 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
 #pragma unroll
                 for (int q = 0; q < NMAX; q++) an[q] = a.coef[(int64_t)U.c * a.coef_stride + q];
             }
+            // this thread's rows summed over all M-tiles of the unit, per frequency of
+            // the warp's share; reduced across the rows once per unit
+            float accu[UNIT_RED ? FHP : 1];
+#pragma unroll
+            for (int fi = 0; fi < (UNIT_RED ? FHP : 1); fi++) accu[fi] = 0.f;
             for (int P = 0; 2 * P < U.nmt; P++, m++) {
                 // the rows' phases for both M-tiles, loaded before the wait
                 uint64_t ph0[2] = {0, 0}, pstep[2] = {0, 0};
@@ -463,9 +483,11 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                     const uint64_t ph0_h = h ? ph0[1] : ph0[0];
                     const uint64_t pstep_h = h ? pstep[1] : pstep[0];
                     const bool has = 2 * P + h < U.nmt;
-                    float accf[FHP];
+                    float accf[UNIT_RED ? 1 : FHP];             // per-accumulator reduction only
+                    if constexpr (!UNIT_RED) {
 #pragma unroll
-                    for (int fi = FH; fi < FHP; fi++) accf[fi] = 0.f;
+                        for (int fi = FH; fi < FHP; fi++) accf[fi] = 0.f;
+                    }
                     if (has) {
                         const uint32_t tbase = taddr + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * kTcCols) + hcol;
                         float v[32];
@@ -501,7 +523,11 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                                 }
                                 float acc_c, acc_s;
                                 upk(acc2, acc_c, acc_s);
-                                accf[fi] = live_h ? acc_c + acc_s : 0.f;
+                                if constexpr (UNIT_RED) {
+                                    if (live_h) accu[fi] += acc_c + acc_s;
+                                } else {
+                                    accf[fi] = live_h ? acc_c + acc_s : 0.f;
+                                }
                             } else {
                                 float cp2 = 1.f, sp2 = 0.f, cp1 = c1, sp1 = s1;
                                 float acc = 0.f;
@@ -514,33 +540,49 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                                     cp2 = cp1; sp2 = sp1;
                                     cp1 = cn; sp1 = sn;
                                 }
-                                accf[fi] = live_h ? acc : 0.f;
+                                if constexpr (UNIT_RED) {
+                                    if (live_h) accu[fi] += acc;
+                                } else {
+                                    accf[fi] = live_h ? acc : 0.f;
+                                }
                             }
                         }
                     }
                     // release this accumulator (always, so the phases of both buffers advance per pair)
                     tc_fence_before();
                     mbar_arrive(&bar_tempty[h]);
-                    if (has) {
-                        // sum over the 128 rows, fixed order
-                        const float x = warp_reduce_scatter<FHP>(accf, lane);
-                        constexpr int SH = FHP == 2 ? 4 : FHP == 4 ? 3 : FHP == 8 ? 2 : FHP == 16 ? 1 : 0;
-                        if ((lane & ((1 << SH) - 1)) == 0) s_red[ew][lane >> SH] = x;
-                        asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
-                        if (ew == 0 && lane < FT) {
-                            const int w0 = (lane / FH) * 4, fi = lane % FH;
-                            s_acc[lane] += ((s_red[w0][fi] + s_red[w0 + 1][fi]) + s_red[w0 + 2][fi]) + s_red[w0 + 3][fi];
+                    if constexpr (!UNIT_RED) {
+                        if (has) {
+                            // sum over the 128 rows, fixed order
+                            const float x = warp_reduce_scatter<FHP>(accf, lane);
+                            if ((lane & ((1 << SH) - 1)) == 0) s_red[ew][lane >> SH] = x;
+                            asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
+                            if (ew == 0 && lane < FT) {
+                                const int w0 = (lane / FH) * 4, fi = lane % FH;
+                                s_acc[lane] += ((s_red[w0][fi] + s_red[w0 + 1][fi]) + s_red[w0 + 2][fi]) + s_red[w0 + 3][fi];
+                            }
+                            asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
                         }
-                        asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
                     }
                 }
             }
             if (!ok) break;
-            // unit complete: normalise and emit
+            if constexpr (UNIT_RED) {
+                // unit complete: sum over the rows (lanes, then the four lane groups), fixed order
+                const float x = warp_reduce_scatter<FHP>(accu, lane);
+                if ((lane & ((1 << SH) - 1)) == 0) s_red[ew][lane >> SH] = x;
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
+            }
+            // normalise and emit
             if (ew == 0) {
+                float S = 0.f;
+                if (UNIT_RED && lane < FT) {
+                    const int w0 = (lane / FH) * 4, fi = lane % FH;
+                    S = ((s_red[w0][fi] + s_red[w0 + 1][fi]) + s_red[w0 + 2][fi]) + s_red[w0 + 3][fi];
+                }
                 unsigned long long key = 0ull;
                 if (lane < U.count) {
-                    const float S = s_acc[lane];
+                    if constexpr (!UNIT_RED) S = s_acc[lane];
                     const float v = S * P_.norm;
                     const long long kk = U.kfirst + lane;
                     if (a.stage == kStageFull) {
@@ -560,7 +602,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                             key = make_key(v, (uint32_t)(U.peak * (2 * a.fine_half + 1) + (kk + a.fine_half)));
                     }
                 }
-                s_acc[lane] = 0.f;
+                if constexpr (!UNIT_RED) s_acc[lane] = 0.f;
                 if (a.stage != kStageCoarse) {
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -574,14 +616,14 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
         }
         if (!ok && ew == 0 && lane == 0) atomicOr(a.status, 2);
     } else {
-        // ---------------- Z producers: 256 threads ----------------
-        const int pt = tid - (2 + EW) * 32;           // 0..255
-        const int grp = pt / items;                   // stage group
-        const int it = pt - grp * items;
+        // ---------------- Z producers: PROD threads ----------------
+        const int pt = tid - (2 + EW) * 32;           // 0..PROD-1
+        const int grp = pt / GS;                      // stage group
+        const int it = pt - grp * GS;
         const int g = it & 7;                         // j-octet of the K chunk (fastest: conflict-free stores)
         const int f = (it >> 3) % FT;                 // frequency within the unit
         const int hr = (it >> 3) / FT;                // harmonics hr*NH+1 .. (hr+1)*NH
-        const bool active = grp < groups;
+        const bool active = grp < groups && (GS == items || it < items);
         uint32_t q = 0;
         bool ok = true;
         // After a timeout (ok == false) a producer keeps walking the units so that
@@ -595,14 +637,14 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
             const float* anp = a.coef + (int64_t)U.c * a.coef_stride + hr * NH;   // a_n of this harmonic range
             if (tab) {
                 // every producer is done with the previous unit's table
-                asm volatile("bar.sync 2, 256;" ::: "memory");
-                for (int j = pt; ok && j < U.n; j += kTcProducers) {
+                asm volatile("bar.sync 2, %0;" ::"n"(PROD) : "memory");
+                for (int j = pt; ok && j < U.n; j += PROD) {
                     const uint64_t stp = a.ph_step[off + j];
                     uint64_t ph0 = a.ph_base[off + j] + tc_base_mult<LIST>(a, U) * stp;
                     if (a.stage == kStageFine) ph0 += U.peak_mult * a.ph_coarse[off + j];
                     sPh[tc_tab(j)] = make_ulonglong2(ph0, stp);
                 }
-                asm volatile("bar.sync 2, 256;" ::: "memory");
+                asm volatile("bar.sync 2, %0;" ::"n"(PROD) : "memory");
             }
             for (int P = 0; ok && 2 * P < U.nmt; P++)
                 for (int J = 4 * P; J < U.nkc; J++, q++) {
@@ -653,6 +695,8 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                             cm[r] = pk(ca[0], ca[1]); sm[r] = pk(sa[0], sa[1]);     // n = n0 - 1
                         }
                         unsigned char* Bs = smem + s * kTcStageBytes + 2 * kTcA;
+                        // fully unrolled: measured fastest for every class (a partial unroll
+                        // avoids the 16-harmonic spill but runs slower)
 #pragma unroll
                         for (int nn = 0; nn < NH; nn++) {
                             const int n = hr * NH + 1 + nn;
@@ -673,7 +717,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                             if (nn + 1 < NH) {
 #pragma unroll
                                 for (int r = 0; r < 4; r++) {
-                                    const f2 k = (n & 1) ? km[r] : kp[r];
+                                    const f2 k = (nn & 1) ? kp[r] : km[r];   // n = hr NH + 1 + nn, hr NH even
                                     const f2 cn = fma2(k, cc[r], cm[r]);
                                     const f2 sn = fma2(k, ss[r], sm[r]);
                                     cm[r] = cc[r]; sm[r] = ss[r];
