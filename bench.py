@@ -16,6 +16,9 @@ sigma_t from the Bowley-skewness rule.
   roofline  the pair-sum kernel against the SFU/FP32 pipe ceiling (one ex2 per
             pair-frequency evaluation, 32 ex2/clk/SM)
   cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample
+  tensor    the tensor-core form on the same batch (FP16 or BF16 operands, per-curve
+            harmonics): device-resident rate, its roofline against the measured
+            sustained BF16 rate, the other 16-bit type, and its own e2e
 
 Multi-GPU (torchrun): each rank processes its own batch of the same shape
 (independent lightcurves; no collective on the data path): weak scaling.
@@ -380,6 +383,20 @@ def main():
                          "peak_basis": "bf16 dense sustained, %s (fp16 has the same nominal rate)" % peaks["source"],
                          "avg_launch_ms": float(np.mean(tk_ms))},
         }
+        # the tensor form end to end through the same pinned host buffers
+        if e2e is not None:
+            thplan = cp.Plan(tp, mp, ep, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=cp.CP_FORM_TENSOR,
+                             device=local, stream=stream.cuda_stream, **tkw2)
+            thplan.best_period_into(tidx, tbf, tbs, tper, tps)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(t_steps):
+                thplan.best_period_into(tidx, tbf, tbs, tper, tps)
+            barrier()
+            te_s = max_over_ranks(time.perf_counter() - t0, device=dev)
+            thplan.close()
+            tensor["e2e"] = {"value": world * n * t_steps / te_s, "unit": "lightcurves/s",
+                             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": t_steps}
         # the other 16-bit operand type on the same batch (same plan shape, one timed step)
         other = cp.CP_DTYPE_FP16 if args.dtype == "bf16" else cp.CP_DTYPE_BF16
         oplan = cp.Plan(td, md, ed, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=cp.CP_FORM_TENSOR,
