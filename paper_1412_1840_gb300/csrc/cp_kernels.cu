@@ -265,6 +265,74 @@ __global__ void __launch_bounds__(256) k_build_w(const BuildWArgs a)
 // ===========================================================================
 constexpr int kPairThreads = 512;
 constexpr int kHalfRows = kRowsPerLane / 2;   // rows per lane in a half-tile work item
+// Curves with sigma_t at or above this take the exponent in the cos form (see
+// pair_item); below it the sin form keeps the exponent's rounding relative.
+constexpr float kCosFormMinSigma = 0.3f;
+
+// One work item (16 rows x 32 columns of a tile) at every frequency pair of
+// the unit.  The exponent of the periodic kernel (Eq. (periodickernel)),
+// -beta sin^2(pi dphi) with beta = 2 log2(e) / sigma_t^2, is taken in one of
+// two forms from the trig table of the unit:
+//   sin form  -(c_i s_j - s_i c_j)^2 with (s, c) = (sin, cos)(pi phi) sqrt(beta)
+//             (three f32x2 operations per two frequencies);
+//   cos form  C_i C_j + S_i S_j - beta/2 with (S, C) = (sin, cos)(2 pi phi)
+//             sqrt(beta/2), from sin^2 x = (1 - cos 2x)/2 (two operations).
+// The cos form's rounding is absolute, about beta 2^-24 in the exponent, so it
+// is used only for sigma_t >= kCosFormMinSigma (beta <= 32: below 3e-6 per term).
+template <bool COSF>
+__device__ __forceinline__ void pair_item(const ulonglong2* SC, const f2* NS, int npad, int nfp, int rbase,
+                                          int cbase, f2 nhalf, const f2 (&w01)[kHalfRows],
+                                          const f2 (&w23)[kHalfRows], f2 (&acc)[kFcMax / 2])
+{
+#pragma unroll
+    for (int fp = 0; fp < kFcMax / 2; fp++) {
+        if (fp < nfp) {
+            const ulonglong2* SCf = SC + fp * npad;
+            const f2* NSf = NS + fp * npad;
+            ulonglong2 col[kColsPerLane];
+#pragma unroll
+            for (int m = 0; m < kColsPerLane; m++) col[m] = SCf[cbase + 8 * m];
+            f2 tf0 = 0ull, tf1 = 0ull, tg0 = 0ull, tg1 = 0ull;
+#pragma unroll
+            for (int k = 0; k < kHalfRows; k++) {
+                const int i = rbase + 4 * k;
+                float e[kColsPerLane][2];
+                if (COSF) {
+                    const ulonglong2 R = SCf[i];   // ((S_i(f), S_i(f')), (C_i(f), C_i(f')))
+#pragma unroll
+                    for (int m = 0; m < kColsPerLane; m++) {
+                        const f2 a2 = fma2(R.y, col[m].y, fma2(R.x, col[m].x, nhalf));
+                        float a0, a1;
+                        upk(a2, a0, a1);
+                        e[m][0] = ex2_approx(a0);
+                        e[m][1] = ex2_approx(a1);
+                    }
+                } else {
+                    const f2 A = SCf[i].y;   // (c_i(f), c_i(f'))
+                    const f2 B = NSf[i];     // (-s_i(f), -s_i(f'))
+#pragma unroll
+                    for (int m = 0; m < kColsPerLane; m++) {
+                        const f2 t2 = mul2(B, col[m].y);
+                        const f2 d2 = fma2(A, col[m].x, t2);
+                        const f2 q2 = mul2(d2, d2);
+                        float q0, q1;
+                        upk(q2, q0, q1);
+                        e[m][0] = ex2_approx(-q0);
+                        e[m][1] = ex2_approx(-q1);
+                    }
+                }
+                tf0 = fma2(w01[k], pk(e[0][0], e[1][0]), tf0);
+                tf1 = fma2(w23[k], pk(e[2][0], e[3][0]), tf1);
+                tg0 = fma2(w01[k], pk(e[0][1], e[1][1]), tg0);
+                tg1 = fma2(w23[k], pk(e[2][1], e[3][1]), tg1);
+            }
+            float fx, fy, gx, gy;
+            upk(add2(tf0, tf1), fx, fy);
+            upk(add2(tg0, tg1), gx, gy);
+            acc[fp] = add2(acc[fp], pk(fx + fy, gx + gy));
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs a)
 {
@@ -319,9 +387,11 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
         const int32_t* tl = a.trials + (int64_t)c * a.n_trials;   // list stage only
 
         // trig table: SC[fp][i] = {(s_f, s_f'), (c_f, c_f')} * sqrt(beta), NS[fp][i] = -(s_f, s_f')
+        // (sin form), or the sines and cosines of the doubled angle * sqrt(beta / 2) (cos form)
         ulonglong2* SC = reinterpret_cast<ulonglong2*>(smem);
         f2* NS = reinterpret_cast<f2*>(SC + nfp * npad);
-        const float ts = P.tscale;
+        const bool cosf = P.sigma_t >= kCosFormMinSigma;
+        const float ts = cosf ? P.tscale * P.tscale * 0.70710678f : P.tscale;   // tscale^4 = beta
         for (int it = tid; it < nfp * npad; it += kPairThreads) {
             const int fp = it / npad, i = it - fp * npad;
             ulonglong2 v = make_ulonglong2(0ull, 0ull);
@@ -342,8 +412,13 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
                     ph1 = a.ph_base[off + i] + (uint64_t)k1 * st;
                 }
                 float s0, c0, s1, c1;
-                sincospi_turns((uint32_t)(ph >> 32), s0, c0);
-                sincospi_turns((uint32_t)(ph1 >> 32), s1, c1);
+                if (cosf) {
+                    sincos2pi_turns((uint32_t)(ph >> 32), s0, c0);
+                    sincos2pi_turns((uint32_t)(ph1 >> 32), s1, c1);
+                } else {
+                    sincospi_turns((uint32_t)(ph >> 32), s0, c0);
+                    sincospi_turns((uint32_t)(ph1 >> 32), s1, c1);
+                }
                 s0 *= ts; c0 *= ts; s1 *= ts; c1 *= ts;
                 v = make_ulonglong2(pk(s0, s1), pk(c0, c1));
                 ns = pk(-s0, -s1);
@@ -358,6 +433,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
         const int nitems = 2 * ntiles;           // (tile, row half): 16 x 32 pairs per warp item
         const float4* Wc = reinterpret_cast<const float4*>(a.W + (a.wtile_start[slot] - a.wtile_base) * kTileFloats);
         f2 acc[kFcMax / 2];                      // per f-pair: (sum at f, sum at f')
+        const f2 nhalf = pk(-ts * ts, -ts * ts);   // cos form: -beta/2
 #pragma unroll
         for (int q = 0; q < kFcMax / 2; q++) acc[q] = 0ull;
 
@@ -387,42 +463,8 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
             decode_tile(item >> 1, nb, bi, bj);
             const int rbase = bi * kTile + (item & 1) * (kTile / 2) + la;
             const int cbase = bj * kTile + lb;
-#pragma unroll
-            for (int fp = 0; fp < kFcMax / 2; fp++) {
-                if (fp < nfp) {
-                    const ulonglong2* SCf = SC + fp * npad;
-                    const f2* NSf = NS + fp * npad;
-                    ulonglong2 col[kColsPerLane];
-#pragma unroll
-                    for (int m = 0; m < kColsPerLane; m++) col[m] = SCf[cbase + 8 * m];
-                    f2 tf0 = 0ull, tf1 = 0ull, tg0 = 0ull, tg1 = 0ull;
-#pragma unroll
-                    for (int k = 0; k < kHalfRows; k++) {
-                        const int i = rbase + 4 * k;
-                        const f2 A = SCf[i].y;   // (c_i(f), c_i(f'))
-                        const f2 B = NSf[i];     // (-s_i(f), -s_i(f'))
-                        float e[kColsPerLane][2];
-#pragma unroll
-                        for (int m = 0; m < kColsPerLane; m++) {
-                            const f2 t2 = mul2(B, col[m].y);
-                            const f2 d2 = fma2(A, col[m].x, t2);
-                            const f2 q2 = mul2(d2, d2);
-                            float q0, q1;
-                            upk(q2, q0, q1);
-                            e[m][0] = ex2_approx(-q0);
-                            e[m][1] = ex2_approx(-q1);
-                        }
-                        tf0 = fma2(w01[k], pk(e[0][0], e[1][0]), tf0);
-                        tf1 = fma2(w23[k], pk(e[2][0], e[3][0]), tf1);
-                        tg0 = fma2(w01[k], pk(e[0][1], e[1][1]), tg0);
-                        tg1 = fma2(w23[k], pk(e[2][1], e[3][1]), tg1);
-                    }
-                    float fx, fy, gx, gy;
-                    upk(add2(tf0, tf1), fx, fy);
-                    upk(add2(tg0, tg1), gx, gy);
-                    acc[fp] = add2(acc[fp], pk(fx + fy, gx + gy));
-                }
-            }
+            if (cosf) pair_item<true>(SC, NS, npad, nfp, rbase, cbase, nhalf, w01, w23, acc);
+            else pair_item<false>(SC, NS, npad, nfp, rbase, cbase, nhalf, w01, w23, acc);
         }
 
         // warp reduction of the 2*nfp frequency sums, then a fixed-order CTA sum

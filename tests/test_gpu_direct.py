@@ -85,6 +85,21 @@ def test_ragged_batch_periodogram_rule_sigma_t(f_min):
     check_best(best, ref)
 
 
+@pytest.mark.parametrize("sigma_t", [0.12, 0.29, 0.3, 0.45, 0.6])
+def test_exponent_forms_meet_the_bar(sigma_t):
+    """Below sigma_t = 0.3 the kernel takes the exponent in the sin form, from
+    0.3 on in the cos form, whose rounding (absolute, ~beta 2^-24) is largest at
+    0.3; long curves (N 700-1000) give the longest sums."""
+    b = synth.ragged_batch(4, seed=31, n_lo=700, n_hi=1000)
+    g = synth.Grid(0.002, 1e-4, 200)
+    out, best, stats, _ = run_gpu(b, g, sigma_t=sigma_t)
+    ref = oracle.batch_nckp(b, np.full(b.n_curves, sigma_t), g.freqs())
+    err = peak_rel_err(out, ref)
+    print("sigma_t %.2f: max peak-relative error %.2e" % (sigma_t, err.max()))
+    assert np.all(err <= TOL), err
+    check_best(best, ref)
+
+
 def test_curve_stats_match_oracle():
     b = synth.ragged_batch(24, seed=22, n_lo=2, n_hi=700)
     g = synth.Grid(0.01, 0.01, 40)
