@@ -24,7 +24,7 @@
  *   - coarse-then-fine search      top-k local maxima of a coarse grid,
  *                                  each refined on a fine window
  *
- * Readings where the paper is silent (all also listed in the design doc):
+ * Readings where the paper is silent:
  *   median of an even count = mean of the two middle values;
  *   iqr(y) for pSNR = Q3 - Q1 with quantiles by linear interpolation between
  *     order statistics (position q*(N-1));

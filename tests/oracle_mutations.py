@@ -31,7 +31,10 @@ results = []
 for name, old, new in muts:
     if os.path.exists(DST):
         shutil.rmtree(DST)
-    shutil.copytree(SRC, DST, ignore=shutil.ignore_patterns('.git', '_work', 'gpurun_out', '*.so', '_lib', '__pycache__'))
+    # the oracle, the input generators and the tests: all a pin needs
+    for d in ('oracle', 'synth', 'tests'):
+        shutil.copytree(os.path.join(SRC, d), os.path.join(DST, d),
+                        ignore=shutil.ignore_patterns('*.so', '__pycache__'))
     p = os.path.join(DST, 'oracle', 'ckp_oracle.c')
     s = open(p).read()
     assert s.count(old) == 1, name
