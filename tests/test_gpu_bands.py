@@ -77,6 +77,7 @@ def check_trials(b, g, dev_idx, rows, min_exact=0.98):
             exact += int(np.sum(dk == rk))
             total += nt
     assert total > 0
+    print("trial lists: %d of %d entries identical to the oracle's" % (exact, total))
     assert exact >= min_exact * total, (exact, total)
     return ref
 
