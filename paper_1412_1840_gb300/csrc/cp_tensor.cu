@@ -209,6 +209,13 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&x)[FT], int lane)
     return v;
 }
 
+template <bool SFU>
+__device__ __forceinline__ void epi_sincos(uint32_t U, float& s, float& c)
+{
+    if (SFU) sincos2pi_turns_sfu(U, s, c);
+    else sincos2pi_turns(U, s, c);
+}
+
 // ===========================================================================
 // k_pair_tensor
 // ===========================================================================
@@ -321,6 +328,9 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     // the M-tiles) or once per accumulator; the latter measured faster only for
     // 16 harmonics, where the former raises register spills.
     constexpr bool UNIT_RED = NMAX != 16;
+    // Epilogue angles by the SFU approximations (absolute error ~1e-6, far below the
+    // 16-bit rounding of Z); kept exact where the SFU form raised register spills.
+    constexpr bool EPI_SFU = NMAX == 4 || NMAX == 8 || NMAX == 16;
     // a producer's harmonic range starts at n0 = hr NH + 1 with sigma_{n0-1} = sigma_{n0} = +
     static_assert(!FOLD || HS == 1 || NH % 4 == 0, "harmonic ranges must start on the sign pattern's period");
     static_assert(!FOLD || NH % 2 == 0, "the producers take the step's sign from the parity of nn");
@@ -493,13 +503,13 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                         float v[32];
                         // the angle of odd frequencies is the even one's rotated by one frequency step
                         float sr = 0.f, cr = 1.f, s1 = 0.f, c1 = 0.f;
-                        if (live_h) sincos2pi_turns((uint32_t)(pstep_h >> 32), sr, cr);
+                        if (live_h) epi_sincos<EPI_SFU>((uint32_t)(pstep_h >> 32), sr, cr);
 #pragma unroll
                         for (int fi = 0; fi < FH; fi++) {
                             const int f = fh * FH + fi;       // FH is even: f and fi have the same parity
                             if (live_h) {
                                 if ((fi & 1) == 0 || list) {
-                                    sincos2pi_turns((uint32_t)((ph0_h + tc_mult<LIST>(a, U, f) * pstep_h) >> 32), s1, c1);
+                                    epi_sincos<EPI_SFU>((uint32_t)((ph0_h + tc_mult<LIST>(a, U, f) * pstep_h) >> 32), s1, c1);
                                 } else {
                                     const float cn = fmaf(c1, cr, -s1 * sr), sn = fmaf(s1, cr, c1 * sr);
                                     c1 = cn;
