@@ -1,7 +1,8 @@
-"""Plants plausible mistakes in a copy of the oracle's bands-method,
-preprocessing and whitening code and checks that the pin tests catch each
-one (run by hand: python tests/oracle_mutations.py; a few minutes on CPU).
-Every mistake must make at least one pin fail."""
+"""Plants plausible mistakes in a copy of the oracle -- the statistic and its
+kernels, the order statistics, the sigma_t rule, the thresholds, the searches,
+the bands method, preprocessing and whitening -- and checks that the pin tests
+catch each one (run by hand: python tests/oracle_mutations.py; some minutes on
+CPU).  Every mistake must make at least one pin fail."""
 import os
 import shutil
 import subprocess
@@ -26,9 +27,35 @@ muts = [
  ("whiten: window not circular", "q = ((q % n) + n) % n;", "q = q < 0 ? 0 : (q >= n ? n - 1 : q);"),
  ("whiten: phase of t times P0", "double q = t[i] / p0;", "double q = t[i] * p0;"),
 ]
+core = [
+ ("gauss: 2 sigma^2 -> sigma^2", "return exp(-(x * x) / (2.0 * sigma * sigma)) / (sqrt(2.0 * ORC_PI) * sigma);",
+  "return exp(-(x * x) / (sigma * sigma)) / (sqrt(2.0 * ORC_PI) * sigma);"),
+ ("gauss: normalisation sqrt(2 pi sigma)", "return exp(-(x * x) / (2.0 * sigma * sigma)) / (sqrt(2.0 * ORC_PI) * sigma);",
+  "return exp(-(x * x) / (2.0 * sigma * sigma)) / sqrt(2.0 * ORC_PI * sigma);"),
+ ("periodic kernel: sin(2 pi f dt)", "double s = sin(ORC_PI * f * dt);", "double s = sin(2.0 * ORC_PI * f * dt);"),
+ ("periodic kernel: factor 2 dropped", "return exp(-2.0 * s * s / (sigma * sigma))", "return exp(-s * s / (sigma * sigma))"),
+ ("IP: divided by N", "    return acc / ((double)n * (double)n);\n}\n\n/* Eq. (HP)", "    return acc / (double)n;\n}\n\n/* Eq. (HP)"),
+ ("CKP: upper triangle only", "            for (int64_t j = 0; j < n; j++)\n                acc += (orc_gauss(y[i] - y[j]",
+  "            for (int64_t j = i + 1; j < n; j++)\n                acc += (orc_gauss(y[i] - y[j]"),
+ ("batch CKP: upper triangle only", "            for (int64_t j = 0; j < n; j++)\n                acc += (orc_gauss((double)mags",
+  "            for (int64_t j = i + 1; j < n; j++)\n                acc += (orc_gauss((double)mags"),
+ ("CKP: + IP", "sigma_y) - ip) *", "sigma_y) + ip) *"),
+ ("nCKP: sqrt(N / sigma_t)", "sqrt((double)n * sigma_t) / ip", "sqrt((double)n / sigma_t) / ip"),
+ ("median: upper middle value", "return 0.5 * (s[n / 2 - 1] + s[n / 2]);", "return s[n / 2];"),
+ ("quantile: position q N", "double pos = q * (double)(n - 1);", "double pos = q * (double)n;"),
+ ("pSNR: alpha dropped", "return 0.7413 * iqr / (alpha * orc_median(e, n));", "return 0.7413 * iqr / orc_median(e, n);"),
+ ("Bowley: q3 - q1 in the numerator", "return (q3 + q1 - 2.0 * q2) / (q3 - q1);", "return (q3 - q1 - 2.0 * q2) / (q3 - q1);"),
+ ("sigma_t rule: S instead of S^2", "return 0.1 + 0.5 * exp(-12.0 * sk * sk);", "return 0.1 + 0.5 * exp(-12.0 * sk);"),
+ ("thresholds: bins right-closed", "if (psnr >= ORC_BIN_LO[k])", "if (psnr > ORC_BIN_LO[k])"),
+ ("thresholds: digits swapped", "1.1153", "1.1513"),
+ ("argmax: ties to the highest index", "if (v[k] > v[b])", "if (v[k] >= v[b])"),
+ ("coarse maxima: non-strict left neighbour", "int left_ok = (k == 0) || (v[k] > v[k - 1]);", "int left_ok = (k == 0) || (v[k] >= v[k - 1]);"),
+ ("fine window: half-width in coarse steps", "floor(g->fine_halfwidth / g->fine_df + 0.5)", "floor(g->fine_halfwidth / g->coarse_df + 0.5)"),
+]
 tests = ["tests/test_oracle_bands.py", "tests/test_oracle_prep.py", "tests/test_oracle_whiten.py"]
+core_tests = ["tests/test_oracle_pins.py"]
 results = []
-for name, old, new in muts:
+for name, old, new, tfiles in [m + (core_tests,) for m in core] + [m + (tests,) for m in muts]:
     if os.path.exists(DST):
         shutil.rmtree(DST)
     # the oracle, the input generators and the tests: all a pin needs
@@ -39,7 +66,7 @@ for name, old, new in muts:
     s = open(p).read()
     assert s.count(old) == 1, name
     open(p, 'w').write(s.replace(old, new))
-    r = subprocess.run([sys.executable, '-m', 'pytest', '-x', '-q', '-p', 'no:cacheprovider'] + tests, cwd=DST,
+    r = subprocess.run([sys.executable, '-m', 'pytest', '-x', '-q', '-p', 'no:cacheprovider'] + tfiles, cwd=DST,
                        capture_output=True, text=True, timeout=600)
     caught = r.returncode != 0
     failed = [l for l in r.stdout.splitlines() if l.startswith('FAILED')]

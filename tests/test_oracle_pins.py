@@ -184,7 +184,11 @@ def test_bowley_skewness_and_sigma_t_rule():
     assert oracle.bowley_skewness(np.array([1, 1, 1, 1, 2, 10.0])) == pytest.approx(1.0)
     assert oracle.sigma_t_rule(np.array([1, 1, 1, 1, 2, 10.0])) == pytest.approx(0.1 + 0.5 * math.exp(-12), rel=1e-14)
     # odd N, middle excluded: [1,2,3,4,100] -> Q1 = 1.5, Q3 = 52, Q2 = 3
-    assert oracle.bowley_skewness(np.array([1, 2, 3, 4, 100.0])) == pytest.approx((52 + 1.5 - 6) / 50.5, rel=1e-14)
+    S = (52 + 1.5 - 6) / 50.5
+    assert oracle.bowley_skewness(np.array([1, 2, 3, 4, 100.0])) == pytest.approx(S, rel=1e-14)
+    # the rule at an S other than 0 and +-1 (where S and S^2 agree)
+    assert oracle.sigma_t_rule(np.array([1, 2, 3, 4, 100.0])) == pytest.approx(0.1 + 0.5 * math.exp(-12 * S * S),
+                                                                                rel=1e-14)
     # mirrored data flips the sign; constant data gives 0 (Q3 == Q1)
     x = np.random.default_rng(1).lognormal(size=101)
     assert oracle.bowley_skewness(-x) == pytest.approx(-oracle.bowley_skewness(x), rel=1e-14)
@@ -248,6 +252,42 @@ def test_hierarchical_reduces_to_full_grid():
     # the two routes reach the same grid frequency up to one FP64 ulp (f_min + k df versus
     # f_peak + j fine_df); over a 300-day span that ulp moves nCKP by ~1e-13 relative
     np.testing.assert_allclose(hier["best_stat"], full["best_stat"], rtol=1e-12)
+
+
+def test_hierarchical_search_by_brute_force():
+    """Coarse-then-fine search with a fine step finer than the coarse one: the
+    result equals the search composed by hand from pinned pieces -- nCKP on the
+    coarse grid, its top-k local maxima, windows of +-round(halfwidth / fine_df)
+    fine steps clipped to [f_min, f_max], the best value over all windows."""
+    b = synth.ragged_batch(3, seed=13, n_lo=30, n_hi=60, span=400.0)
+    g = synth.Grid(0.01, 1e-3, 991, True, 5e-3, 3, 1e-3, 4e-3)     # f_max = 1.0
+    r = oracle.batch_best(b, g, sigma_t=0.3)
+    kc = int(np.floor((g.f_max - g.f_min) / g.coarse_df + 0.5)) + 1
+    J = int(np.floor(g.fine_halfwidth / g.fine_df + 0.5))
+    assert J == 4
+    for c in range(b.n_curves):
+        t, m, e = b.curve(c)
+        y, sy = m.astype(np.float64), oracle.median(e.astype(np.float64))
+        fc = g.f_min + np.arange(kc) * g.coarse_df
+        peaks = oracle.top_local_maxima(oracle.nckp(t, y, sy, 0.3, fc), g.top_k)
+        cand = [g.f_min + p * g.coarse_df + j * g.fine_df for p in peaks for j in range(-J, J + 1)]
+        cand = np.array([f for f in cand if g.f_min <= f <= g.f_max])
+        v = oracle.nckp(t, y, sy, 0.3, cand)
+        assert r["best_freq"][c] == cand[int(np.argmax(v))]
+        assert r["best_stat"][c] == pytest.approx(v.max(), rel=1e-13)
+
+
+def test_batch_nckp_equals_single_curve_nckp():
+    """The batch evaluation (per-curve sigma_t, float32 inputs widened) is the
+    single-curve Eq. (CKP) evaluation curve by curve."""
+    b = synth.ragged_batch(4, seed=14, n_lo=2, n_hi=50, span=600.0)
+    st = np.array([0.15, 0.3, 0.45, 0.6])
+    fr = np.linspace(0.01, 2.0, 37)
+    got = oracle.batch_nckp(b, st, fr)
+    for c in range(b.n_curves):
+        t, m, e = b.curve(c)
+        ref = oracle.nckp(t, m.astype(np.float64), oracle.median(e.astype(np.float64)), st[c], fr)
+        np.testing.assert_allclose(got[c], ref, rtol=1e-13, atol=1e-15)
 
 
 def test_noiseless_sinusoid_recovered_within_one_step():
