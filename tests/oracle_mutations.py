@@ -51,11 +51,17 @@ core = [
  ("argmax: ties to the highest index", "if (v[k] > v[b])", "if (v[k] >= v[b])"),
  ("coarse maxima: non-strict left neighbour", "int left_ok = (k == 0) || (v[k] > v[k - 1]);", "int left_ok = (k == 0) || (v[k] >= v[k - 1]);"),
  ("fine window: half-width in coarse steps", "floor(g->fine_halfwidth / g->fine_df + 0.5)", "floor(g->fine_halfwidth / g->coarse_df + 0.5)"),
+ ("sigma_y: largest error bar", "    double sy = orc_median(e, n);\n    double st = curve_sigma_t(o, y, n, c);",
+  "    double sy = orc_quantile(e, n, 1.0);\n    double st = curve_sigma_t(o, y, n, c);"),
+ ("discriminator: flipped", "r->is_periodic = r->best_stat > orc_threshold(r->psnr);", "r->is_periodic = r->best_stat < orc_threshold(r->psnr);"),
 ]
 tests = ["tests/test_oracle_bands.py", "tests/test_oracle_prep.py", "tests/test_oracle_whiten.py"]
 core_tests = ["tests/test_oracle_pins.py"]
 results = []
+only = sys.argv[1:]            # optional name prefixes: run just those mutations
 for name, old, new, tfiles in [m + (core_tests,) for m in core] + [m + (tests,) for m in muts]:
+    if only and not any(name.startswith(o) for o in only):
+        continue
     if os.path.exists(DST):
         shutil.rmtree(DST)
     # the oracle, the input generators and the tests: all a pin needs
