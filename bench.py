@@ -290,7 +290,7 @@ def main():
     value = world * n * args.steps / total_s
     plan.close()
 
-    # ---- per-curve transforms around the search (Sections 5.1 and 7.1) ----
+    # ---- per-curve transforms around the search (Sections 5.2 and 7.1) ----
     transforms = None
     if not args.no_transforms:
         def timed_ms(fn, reps=3):

@@ -38,7 +38,7 @@ typedef enum {
     CP_EINVAL = 1,       /* invalid argument or input value (see cp_last_error)      */
     CP_ENOMEM = 2,       /* device or pinned host allocation failed                  */
     CP_ECUDA = 3,        /* CUDA runtime / driver error                              */
-    CP_ETIMEOUT = 4,     /* a bounded device wait gave up (reserved; no waits today) */
+    CP_ETIMEOUT = 4,     /* a bounded device wait of a tensor-form kernel gave up     */
     CP_ESTATE = 5,       /* plan used in a state that does not allow the call        */
     CP_EUNSUPPORTED = 6  /* valid request the build does not support (e.g. N > max)  */
 } cp_status;
@@ -227,7 +227,7 @@ cp_status cp_curve_stats(cp_plan_t plan, float *sigma_y, float *sigma_t, double 
 cp_status cp_trial_frequencies(cp_plan_t plan, int32_t *trial_idx, float *trial_stat);
 
 /*
- * cp_preprocess -- the cleaning of Section 5.1 on the device, for a batch
+ * cp_preprocess -- the cleaning of Section 5.2 on the device, for a batch
  * before it is planned: samples whose error bar is not below
  * mean(e) + 3 std(e) (population std, per curve) are dropped; curves with
  * fewer than min_n samples left (50 in the paper) are discarded; the

@@ -181,7 +181,7 @@ def top_local_maxima(v, top_k) -> np.ndarray:
     return out[:n]
 
 
-# ---- preprocessing, Section 5.1 --------------------------------------------
+# ---- preprocessing, Section 5.2 --------------------------------------------
 
 
 def chi2_line(t, x, e):

@@ -472,7 +472,7 @@ static int cmp_rank_item(const void *a, const void *b)
 
 /* Step 2: ten bands of equal sample count on the magnitude axis.  Band k
  * holds the samples of magnitude rank r with floor(kN/10) <= r < floor((k+1)N/10)
- * (rank 0 = faintest value, i.e. smallest magnitude number; equal magnitudes
+ * (rank 0 = smallest magnitude number, i.e. the brightest value; equal magnitudes
  * ranked by sample index). */
 void orc_bands_of(const double *y, int64_t n, int32_t *band)
 {
@@ -621,7 +621,7 @@ void orc_batch_bands_trials(const double *times, const float *mags, const int64_
 }
 
 /* ---------------------------------------------------------------------- */
-/* Preprocessing, Section 5.1                                              */
+/* Preprocessing, Section 5.2                                              */
 /* ---------------------------------------------------------------------- */
 
 typedef struct {

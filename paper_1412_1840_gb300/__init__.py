@@ -382,7 +382,7 @@ def _device_tensor(a, name):
 
 
 def cp_preprocess(times, mags, errs, offsets, min_n=50, stream=None):
-    """Section 5.1 cleaning on the device (see include/cp.h).  times (float64),
+    """Section 5.2 cleaning on the device (see include/cp.h).  times (float64),
     mags and errs (float32) are CUDA tensors; offsets a host int64 array.
     Returns a dict: the kept samples ``times``, ``mags``, ``errs`` (CUDA
     tensors), ``offsets`` over the kept curves (host), ``curve`` (input index

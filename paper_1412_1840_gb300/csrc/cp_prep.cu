@@ -1,7 +1,7 @@
 // cp_prep.cu -- per-curve transforms around the periodogram search
 // (arXiv:1412.1840):
 //
-//   cp_preprocess  Section 5.1: drop samples whose error bar is not below
+//   cp_preprocess  Section 5.2: drop samples whose error bar is not below
 //                  mean(e) + 3 std(e) (population std), discard curves with
 //                  fewer than min_n samples left, fit x = a0 + a1 t by the
 //                  weighted linear chi^2 of Eq. (chisquare) and subtract the

@@ -26,6 +26,11 @@ muts = [
  ("whiten: window shifted by one", "int64_t q = k - w / 2 + j;", "int64_t q = k - w / 2 + j + 1;"),
  ("whiten: window not circular", "q = ((q % n) + n) % n;", "q = q < 0 ? 0 : (q >= n ? n - 1 : q);"),
  ("whiten: phase of t times P0", "double q = t[i] / p0;", "double q = t[i] * p0;"),
+ ("whiten batch: output of later curves shifted", "orc_whiten(times + a, x, n, p0[c], w, out + a);",
+  "orc_whiten(times + a, x, n, p0[c], w, out + (c > 0 ? a - 1 : a));"),
+ ("whiten batch: period guard inverted", "if (p0[c] > 0.0 && isfinite(p0[c]))", "if (!(p0[c] > 0.0 && isfinite(p0[c])))"),
+ ("whiten batch: zero period whitened", "if (p0[c] > 0.0 && isfinite(p0[c]))", "if (p0[c] >= 0.0 && isfinite(p0[c]))"),
+ ("whiten batch: infinite period whitened", "if (p0[c] > 0.0 && isfinite(p0[c]))", "if (p0[c] > 0.0 && !isnan(p0[c]))"),
 ]
 core = [
  ("gauss: 2 sigma^2 -> sigma^2", "return exp(-(x * x) / (2.0 * sigma * sigma)) / (sqrt(2.0 * ORC_PI) * sigma);",

@@ -1,4 +1,4 @@
-"""Parity of the device preprocessing (Section 5.1) and whitening
+"""Parity of the device preprocessing (Section 5.2) and whitening
 (Section 7.1) with the FP64 oracle, and the two-level multimode search."""
 import numpy as np
 import pytest

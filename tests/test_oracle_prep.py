@@ -1,4 +1,4 @@
-"""Pins of the oracle's preprocessing (Section 5.1): error-bar cut
+"""Pins of the oracle's preprocessing (Section 5.2): error-bar cut
 e_i < mean(e) + 3 std(e), discard below 50 samples, weighted linear chi^2
 fit of Eq. (chisquare) removed when corr(x, fit) > 0.5 -- against closed
 forms and independent library routines."""

@@ -48,3 +48,32 @@ def test_short_curve_uses_all_samples():
     t = np.array([0.1, 0.5, 1.3, 2.2])
     x = np.array([1.0, 2.0, 4.0, 8.0])
     np.testing.assert_allclose(oracle.whiten(t, x, 1.0), x - x.mean(), atol=1e-15)
+
+
+def test_batch_whitening_matches_single_curves_and_passes_bad_periods_through():
+    """The batch driver against the pinned single-curve whitening: every
+    curve of a ragged CSR batch lands at its own offsets, and a curve whose
+    period is <= 0, NaN or infinite comes back unchanged (FP32 magnitudes
+    widened exactly)."""
+    import synth
+    rng = np.random.default_rng(3)
+    sizes = [45, 7, 120, 31, 2, 66, 30, 89]
+    t_parts, m_parts = [], []
+    for n in sizes:
+        t = np.sort(rng.uniform(0.0, 1500.0, n))
+        t_parts.append(t)
+        m_parts.append((16.0 + 0.4 * np.sin(2 * np.pi * t / 3.3) + rng.normal(0, 0.05, n)).astype(np.float32))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    b = synth.Batch(np.concatenate(t_parts), np.concatenate(m_parts), np.ones(off[-1], np.float32), off,
+                    np.zeros(len(sizes)), np.zeros(len(sizes), bool), np.zeros(len(sizes), np.int8))
+    p0 = np.array([3.3, 0.0, 7.9, -2.0, 1.1, np.nan, np.inf, 0.61])
+    out = oracle.batch_whiten(b, p0, w=30)
+    assert out.shape == (off[-1],)
+    for c, n in enumerate(sizes):
+        t, m, _ = b.curve(c)
+        got = out[off[c]:off[c + 1]]
+        if p0[c] > 0 and np.isfinite(p0[c]):
+            np.testing.assert_array_equal(got, oracle.whiten(t, m.astype(np.float64), p0[c], 30))
+            assert n < 3 or np.any(got != m)
+        else:
+            np.testing.assert_array_equal(got, m.astype(np.float64))
