@@ -348,26 +348,38 @@ def cp_trial_frequencies(plan: Plan):
 def cp_best_period_noalloc(times, mags, errs, offsets, grid: cp_freq_grid, sigma_t: float, best_idx=None,
                            best_freq=None, best_stat=None, is_periodic=None, stream=None):
     """Best-period search that allocates no device memory (for callers that
-    cannot allocate at call time).  Inputs and outputs are CUDA tensors on
-    the current device (outputs: int64, float64, float32, uint8; any may be
-    None); offsets is a host int64 array.  Synchronous."""
-    pt, dt, _ = _ptr(times)
-    pm, dm, _ = _ptr(mags)
-    pe, de, _ = _ptr(errs)
-    if not (dt and dm and de):
-        raise ValueError("times, mags and errs must be CUDA tensors")
+    cannot allocate at call time).  Inputs and outputs are contiguous CUDA
+    tensors on the current device: times float64, mags and errs float32 with
+    offsets[-1] elements; outputs int64, float64, float32, uint8 with
+    n_curves elements (any may be None).  offsets is a host int64 array.
+    Synchronous.  Arguments of the wrong type, size or device raise
+    ValueError before anything reaches the GPU."""
+    import torch
     off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    if off.ndim != 1 or off.shape[0] < 2:
+        raise ValueError("offsets must hold n_curves + 1 entries")
+    n_pts, n_cur = int(off[-1]), int(off.shape[0] - 1)
+    cur = torch.cuda.current_device()
+
+    def dev_arg(a, name, dtype, count):
+        if not (isinstance(a, torch.Tensor) and a.is_cuda):
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if a.device.index != cur:
+            raise ValueError("%s is on cuda:%s, the current device is cuda:%d" % (name, a.device.index, cur))
+        if a.dtype != dtype:
+            raise ValueError("%s must be %s, not %s" % (name, dtype, a.dtype))
+        if not a.is_contiguous() or a.numel() != count:
+            raise ValueError("%s must be contiguous with %d elements (it has %d)" % (name, count, a.numel()))
+        return a.data_ptr()
+
+    pt = dev_arg(times, "times", torch.float64, n_pts)
+    pm = dev_arg(mags, "mags", torch.float32, n_pts)
+    pe = dev_arg(errs, "errs", torch.float32, n_pts)
     outs = []
-    for o in (best_idx, best_freq, best_stat, is_periodic):
-        if o is None:
-            outs.append(None)
-            continue
-        po, on_dev, _ = _ptr(o)
-        if not on_dev:
-            raise ValueError("outputs must be CUDA tensors")
-        outs.append(po)
+    for o, name, dt in ((best_idx, "best_idx", torch.int64), (best_freq, "best_freq", torch.float64),
+                        (best_stat, "best_stat", torch.float32), (is_periodic, "is_periodic", torch.uint8)):
+        outs.append(None if o is None else dev_arg(o, name, dt, n_cur))
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream().cuda_stream
     _check(_load().cp_best_period_noalloc(pt, pm, pe, off.ctypes.data, int(off.shape[0] - 1), ctypes.byref(grid),
                                           float(sigma_t), ctypes.c_void_p(stream) if stream else None, *outs),

@@ -467,11 +467,9 @@ size_t window_smem_bytes(int max_band_points, int n_t) { return win_layout(max_b
 
 cudaError_t prepare_bands_kernels(int np2max, int max_band_points, int n_t)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_bands, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bands_smem_bytes(np2max));
+    cudaError_t e = raise_dyn_smem((const void*)k_bands, bands_smem_bytes(np2max));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)window_smem_bytes(max_band_points, n_t));
+    return raise_dyn_smem((const void*)k_window, window_smem_bytes(max_band_points, n_t));
 }
 
 cudaError_t launch_bands(const BandsArgs& a, int n_curves, cudaStream_t s)

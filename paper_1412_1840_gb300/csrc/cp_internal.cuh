@@ -251,6 +251,12 @@ cudaError_t pair_direct_occupancy(int* blocks_per_sm, size_t smem);
 size_t stats_smem_bytes(int np2max);
 cudaError_t prepare_kernels(int np2max, size_t pair_smem);
 
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`; never lowers it.  The limit is process-wide per device, so
+// a plan (or another entry point) that needs less must not shrink the limit
+// that an earlier plan's launches rely on.
+cudaError_t raise_dyn_smem(const void* func, size_t bytes);
+
 // Thread-local message returned by cp_last_error() (fixed buffer, no heap).
 cp_status set_error(cp_status s, const char* msg);
 const char* last_error_buffer();

@@ -11,6 +11,9 @@
 //                  (the bands method of Section 3.1 is in cp_bands.cu)
 //   k_finalize     best frequency, nCKP and Table tab:th discriminator
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "cp_internal.cuh"
@@ -653,17 +656,34 @@ int pair_direct_threads() { return kPairThreads; }
 
 size_t stats_smem_bytes(int np2max) { return (size_t)np2max * (sizeof(double) + 3 * sizeof(float)); }
 
+namespace {
+std::mutex g_smem_mutex;
+std::map<std::pair<const void*, int>, size_t> g_smem_limit;   // (kernel, device) -> limit set
+}  // namespace
+
+cudaError_t raise_dyn_smem(const void* func, size_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_smem_mutex);
+    size_t& cur = g_smem_limit[std::make_pair(func, dev)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 cudaError_t prepare_kernels(int np2max, size_t pair_smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_stats, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)stats_smem_bytes(np2max));
+    cudaError_t e = raise_dyn_smem((const void*)k_stats, stats_smem_bytes(np2max));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_pair_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem);
+    return raise_dyn_smem((const void*)k_pair_direct, pair_smem);
 }
 
 cudaError_t pair_direct_occupancy(int* blocks_per_sm, size_t smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_dyn_smem((const void*)k_pair_direct, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pair_direct, kPairThreads, smem);
 }

@@ -64,6 +64,21 @@ cp_status scratch_base(int dev, void** out)
     return CP_OK;
 }
 
+// Waits for the stream when a call fails after it has queued work: the
+// kernels already in flight write to the shared scratch array, and a retry
+// (or the next call, on any stream) must not start while they run.
+struct SyncOnError {
+    cudaStream_t s;
+    bool armed;
+    ~SyncOnError()
+    {
+        if (armed) {
+            cudaStreamSynchronize(s);
+            cudaGetLastError();
+        }
+    }
+};
+
 struct Carve {
     char* base;
     size_t used;
@@ -101,14 +116,40 @@ extern "C" cp_status cp_best_period_noalloc(const double* times, const float* ma
     if (g.hierarchical != CP_SEARCH_FULL && g.hierarchical != CP_SEARCH_COARSE_FINE)
         return nfail(CP_EINVAL, "cp_best_period_noalloc: bad search mode");
     if (g.hierarchical) {
-        if (!(g.coarse_df > 0.0 && g.fine_df > 0.0 && g.fine_halfwidth >= 0.0) || g.top_k < 1 || g.top_k > 1024)
+        if (!(g.coarse_df > 0.0 && std::isfinite(g.coarse_df) && g.fine_df > 0.0 && std::isfinite(g.fine_df) &&
+              g.fine_halfwidth >= 0.0 && std::isfinite(g.fine_halfwidth)) ||
+            g.top_k < 1 || g.top_k > 1024)
             return nfail(CP_EINVAL, "cp_best_period_noalloc: bad hierarchical grid");
-        kc = (int64_t)std::floor((f_max - g.f_min) / g.coarse_df + 0.5) + 1;
-        J = (int)std::floor(g.fine_halfwidth / g.fine_df + 0.5);
-        if (J > 1000000 || (2.0 * J + 1.0) * g.top_k > 2e9 || kc > ((int64_t)1 << 31) - 1)
+        // range checks on the doubles, before any conversion to an integer type
+        const double kcd = std::floor((f_max - g.f_min) / g.coarse_df + 0.5) + 1.0;
+        const double jd = std::floor(g.fine_halfwidth / g.fine_df + 0.5);
+        if (!(jd <= 1e6) || (2.0 * jd + 1.0) * g.top_k > 2e9 || !(kcd <= (double)(((int64_t)1 << 31) - 1)))
             return nfail(CP_EINVAL, "cp_best_period_noalloc: hierarchical grid too large");
+        kc = (int64_t)kcd;
+        J = (int)jd;
     }
     if (offsets[0] != 0) return nfail(CP_EINVAL, "cp_best_period_noalloc: offsets[0] must be 0");
+    // inputs and outputs must be device memory of the current device (a host
+    // pointer or a short buffer would otherwise be read or written by the kernels)
+    {
+        int cur = 0;
+        NA_CUDA(cudaGetDevice(&cur));
+        const void* ins[3] = {times, mags, errs};
+        const void* outs[4] = {best_idx, best_freq, best_stat, is_periodic};
+        for (int k = 0; k < 7; k++) {
+            const void* q = k < 3 ? ins[k] : outs[k - 3];
+            if (k >= 3 && !q) continue;
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+                cudaGetLastError();
+                return nfail(CP_EINVAL, "cp_best_period_noalloc: an input or output is not device memory");
+            }
+            if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) ||
+                (at.type == cudaMemoryTypeDevice && at.device != cur))
+                return nfail(CP_EINVAL,
+                             "cp_best_period_noalloc: inputs and outputs must be device memory of the current device");
+        }
+    }
 
     // schedule on the stack: slots by N descending (stable), unit and tile prefix sums
     int32_t order[kMaxCurves];
@@ -189,6 +230,7 @@ extern "C" cp_status cp_best_period_noalloc(const double* times, const float* ma
         return nfail(CP_EUNSUPPORTED, "cp_best_period_noalloc: batch needs more than CP_NOALLOC_SCRATCH_BYTES");
 
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    SyncOnError guard{s, true};
     NA_CUDA(cudaMemcpyAsync(d_cp, cps, nc * sizeof(CurveParams), cudaMemcpyHostToDevice, s));
     NA_CUDA(cudaMemcpyAsync(d_order, order, nc * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     NA_CUDA(cudaMemcpyAsync(d_unit_full, unit_full, (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -320,6 +362,7 @@ extern "C" cp_status cp_best_period_noalloc(const double* times, const float* ma
     unsigned long long status = 0;
     NA_CUDA(cudaMemcpyAsync(&status, d_u64, sizeof(status), cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
+    guard.armed = false;
     if (status) return nfail(CP_EINVAL, "cp_best_period_noalloc: non-finite input, zero median error bar or bad sigma_t");
     return CP_OK;
 }

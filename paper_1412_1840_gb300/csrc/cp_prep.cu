@@ -386,7 +386,7 @@ extern "C" cp_status cp_whiten(const double* times, const float* mags, const int
     PREP_CUDA(cudaMalloc(&d_p0, nc * sizeof(double)));
     PREP_CUDA(cudaMemcpyAsync(d_off, offsets, (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     PREP_CUDA(cudaMemcpyAsync(d_p0, p0, nc * sizeof(double), cudaMemcpyHostToDevice, s));
-    PREP_CUDA(cudaFuncSetAttribute(k_whiten, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PREP_CUDA(raise_dyn_smem((const void*)k_whiten, smem));
     k_whiten<<<(unsigned)nc, kPrepThreads, smem, s>>>(times, mags, d_off, d_p0, window, np2, out_mags);
     PREP_CUDA(cudaGetLastError());
     PREP_CUDA(cudaStreamSynchronize(s));

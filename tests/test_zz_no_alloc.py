@@ -78,3 +78,75 @@ def test_noalloc_limits_are_reported():
     with pytest.raises(cp.CpError) as e:
         cp.cp_best_period_noalloc(dev(b.times), dev(b.mags), dev(b.errs), b.offsets, cp.grid_from(g), 0.3)
     assert e.value.status == cp.CP_EUNSUPPORTED       # more than CP_NOALLOC_MAX_CURVES curves
+
+
+def test_noalloc_does_not_shrink_a_plans_shared_memory():
+    """A plan for long curves, then a no-allocation call on short ones, then
+    the plan's first search: the plan's launches still get the shared
+    memory they were planned with (the limit is process-wide per kernel)."""
+    big = synth.ragged_batch(3, seed=45, n_lo=900, n_hi=1000)
+    small = synth.ragged_batch(4, seed=46, n_lo=20, n_hi=60)
+    g = synth.Grid(0.01, 1e-3, 300)
+    p = cp.Plan(big.times, big.mags, big.errs, big.offsets, cp.grid_from(g), sigma_t=0.3)
+    try:
+        via_noalloc(small, g, 0.3)
+        got = p.best_period()
+    finally:
+        p.close()
+    same(got, via_plan(big, g, 0.3))
+
+
+def test_noalloc_allocates_nothing():
+    """After a first call, a second call changes neither the device's free
+    memory nor what torch's allocator holds (the outputs are allocated by
+    the caller beforehand)."""
+    b = synth.ragged_batch(9, seed=47, n_lo=100, n_hi=500)
+    g = synth.Grid(0.01, 1e-3, 700)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    t, m, e = dev(b.times), dev(b.mags), dev(b.errs)
+    outs = (torch.empty(b.n_curves, dtype=torch.int64, device="cuda"),
+            torch.empty(b.n_curves, dtype=torch.float64, device="cuda"),
+            torch.empty(b.n_curves, dtype=torch.float32, device="cuda"),
+            torch.empty(b.n_curves, dtype=torch.uint8, device="cuda"))
+    cp.cp_best_period_noalloc(t, m, e, b.offsets, cp.grid_from(g), 0.3, *outs)
+    torch.cuda.synchronize()
+    free0, held0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    cp.cp_best_period_noalloc(t, m, e, b.offsets, cp.grid_from(g), 0.3, *outs)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == held0
+
+
+def test_noalloc_rejects_bad_arguments_before_the_gpu():
+    """Wrong dtypes, sizes and host pointers are refused before any kernel
+    runs; so are grids whose refinement width overflows."""
+    import ctypes
+    b = synth.ragged_batch(3, seed=48, n_lo=30, n_hi=40)
+    g = synth.Grid(0.01, 1e-3, 100)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    t, m, e = dev(b.times), dev(b.mags), dev(b.errs)
+    with pytest.raises(ValueError):
+        cp.cp_best_period_noalloc(t.float(), m, e, b.offsets, cp.grid_from(g), 0.3)
+    with pytest.raises(ValueError):
+        cp.cp_best_period_noalloc(t, m[:-1].contiguous(), e, b.offsets, cp.grid_from(g), 0.3)
+    with pytest.raises(ValueError):
+        cp.cp_best_period_noalloc(t, m, e, b.offsets, cp.grid_from(g), 0.3,
+                                  best_stat=torch.empty(b.n_curves + 1, device="cuda"))
+    L = cp.lib()
+    off = np.ascontiguousarray(b.offsets, np.int64)
+    grid = cp.grid_from(g)
+    # host arrays through the C ABI: CP_EINVAL, nothing launched
+    st = L.cp_best_period_noalloc(b.times.ctypes.data, b.mags.ctypes.data, b.errs.ctypes.data, off.ctypes.data,
+                                  b.n_curves, ctypes.byref(grid), ctypes.c_float(0.3), None, None, None, None, None)
+    assert st == cp.CP_EINVAL
+    # a fine step so small that the refinement half-width overflows any integer type
+    bad = cp.make_grid(0.01, 1e-3, 100, hierarchical=True, coarse_df=1e-2, top_k=3, fine_df=1e-300,
+                       fine_halfwidth=1e-3)
+    st = L.cp_best_period_noalloc(t.data_ptr(), m.data_ptr(), e.data_ptr(), off.ctypes.data, b.n_curves,
+                                  ctypes.byref(bad), ctypes.c_float(0.3), None, None, None, None, None)
+    assert st == cp.CP_EINVAL
+    inf = cp.make_grid(0.01, 1e-3, 100, hierarchical=True, coarse_df=1e-2, top_k=3, fine_df=1e-4,
+                       fine_halfwidth=float("inf"))
+    st = L.cp_best_period_noalloc(t.data_ptr(), m.data_ptr(), e.data_ptr(), off.ctypes.data, b.n_curves,
+                                  ctypes.byref(inf), ctypes.c_float(0.3), None, None, None, None, None)
+    assert st == cp.CP_EINVAL
