@@ -294,6 +294,28 @@ int tune_bucket(const cp_tuning& t, int n)
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Failure-injection hook for tests: with CP_FAIL_ALLOC=k in the environment,
+// the k-th allocation (device or pinned host, counted from 1) of one cp_plan
+// call reports cudaErrorMemoryAllocation without allocating.  The plan must
+// then return CP_ENOMEM and release everything it allocated before.
+struct AllocHook {
+    int target = 0, count = 0;
+    AllocHook()
+    {
+        if (const char* env = std::getenv("CP_FAIL_ALLOC")) target = std::atoi(env);
+    }
+    cudaError_t device(void** p, size_t bytes)
+    {
+        if (++count == target) return cudaErrorMemoryAllocation;
+        return cudaMalloc(p, bytes);
+    }
+    cudaError_t pinned(void** p, size_t bytes)
+    {
+        if (++count == target) return cudaErrorMemoryAllocation;
+        return cudaMallocHost(p, bytes);
+    }
+};
+
 // Copies host inputs (pageable case) into the pinned staging buffers.
 void stage_host_inputs(cp_plan_t p)
 {
@@ -985,7 +1007,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     };
     size_t total = 0;
     for (auto& q : parts) total = align_up(total, 256) + q.bytes;
-    CP_CUDA(cudaMalloc(&p->dblock, std::max<size_t>(total, 256)));
+    AllocHook alloc;
+    CP_CUDA(alloc.device(&p->dblock, std::max<size_t>(total, 256)));
     {
         size_t o = 0;
         for (auto& q : parts) {
@@ -1008,7 +1031,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     };
     size_t htotal = 0;
     for (auto& q : hparts) htotal = align_up(htotal, 64) + q.bytes;
-    CP_CUDA(cudaMallocHost(&p->hblock, std::max<size_t>(htotal, 64)));
+    CP_CUDA(alloc.pinned(&p->hblock, std::max<size_t>(htotal, 64)));
     {
         size_t o = 0;
         for (auto& q : hparts) {
