@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-transforms", action="store_true", help="skip timing preprocessing and whitening")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: split ONE batch across the ranks by pair-sum cost (strong scaling) "
+                         "instead of giving every rank its own batch (weak scaling)")
     return ap.parse_args()
 
 
@@ -233,7 +236,7 @@ def main():
         return
     import torch
     import paper_1412_1840_gb300 as cp
-    from paper_1412_1840_gb300.shard import max_over_ranks
+    from paper_1412_1840_gb300.shard import curve_ranges, gather_results, local_csr, max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -245,7 +248,19 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    b, g, name = make_workload(args, rank)
+    shard = None
+    if args.shard:
+        # one global batch (every rank draws the same one), a contiguous curve range per rank
+        full, g, name = make_workload(args, 0)
+        shard = curve_ranges(full.offsets, world)
+        a0, a1 = shard[rank]
+        t_, m_, e_, off_ = local_csr(full.times, full.mags, full.errs, full.offsets, (a0, a1))
+        b = synth.Batch(t_, m_, e_, off_, full.period[a0:a1], full.periodic[a0:a1], full.kind[a0:a1])
+        n_job = full.n_curves
+        del full
+    else:
+        b, g, name = make_workload(args, rank)
+        n_job = world * b.n_curves              # every rank its own batch of the same shape
     form = cp.CP_FORM_TENSOR if args.form == "tensor" else cp.CP_FORM_DIRECT
     grid = cp.grid_from(g)
     stream = torch.cuda.current_stream(dev)
@@ -287,7 +302,7 @@ def main():
     step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
     info = plan.info()
     total_s = max_over_ranks(sum(step_ms) / 1e3, device=dev)
-    value = world * n * args.steps / total_s
+    value = n_job * args.steps / total_s
     plan.close()
 
     # ---- per-curve transforms around the search (Sections 5.2 and 7.1) ----
@@ -332,7 +347,7 @@ def main():
         hplan.close()
         h2d = b.times.nbytes + b.mags.nbytes + b.errs.nbytes
         d2h = idx.nbytes + bf.nbytes + bs.nbytes + per.nbytes + ps.nbytes + 8
-        e2e = {"value": world * n * e_steps / e_s, "unit": "lightcurves/s", "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": n_job * e_steps / e_s, "unit": "lightcurves/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": e_steps}
 
     # ---- tensor-core form on the same resident batch ---------------------
@@ -366,7 +381,7 @@ def main():
         tflops = ti["tensor_flops_search"] / (np.mean(tk_ms) / 1e3) / 1e12
         rel = np.abs(tbs.astype(np.float64) - bs) / np.maximum(np.abs(bs.astype(np.float64)), 1e-30)
         tensor = {
-            "value": world * n * t_steps / t_total, "unit": "lightcurves/s",
+            "value": n_job * t_steps / t_total, "unit": "lightcurves/s",
             "ms_per_step": t_total * 1e3 / t_steps, "steps": t_steps,
             "dtype": args.dtype, "n_max": "per curve (8/12/16/32 by truncation tail <= 1e-4)" if args.n_max == 0
             else args.n_max,
@@ -395,7 +410,7 @@ def main():
             barrier()
             te_s = max_over_ranks(time.perf_counter() - t0, device=dev)
             thplan.close()
-            tensor["e2e"] = {"value": world * n * t_steps / te_s, "unit": "lightcurves/s",
+            tensor["e2e"] = {"value": n_job * t_steps / te_s, "unit": "lightcurves/s",
                              "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": t_steps}
         # the other 16-bit operand type on the same batch (same plan shape, one timed step)
         other = cp.CP_DTYPE_FP16 if args.dtype == "bf16" else cp.CP_DTYPE_BF16
@@ -413,10 +428,15 @@ def main():
         oplan.close()
         orel = np.abs(tbs.astype(np.float64) - bs) / np.maximum(np.abs(bs.astype(np.float64)), 1e-30)
         tensor["other_dtype"] = {"dtype": "fp16" if other == cp.CP_DTYPE_FP16 else "bf16",
-                                 "value": world * n / o_s, "unit": "lightcurves/s", "ms_per_step": o_s * 1e3,
+                                 "value": n_job / o_s, "unit": "lightcurves/s", "ms_per_step": o_s * 1e3,
                                  "best_idx_agreement_vs_direct": float(np.mean(tidx == idx)),
                                  "best_stat_max_rel_diff_vs_direct": float(orel.max())}
 
+    gathered = None
+    if shard is not None:
+        # every rank's best periods, in global curve order (host-side, after the timed region)
+        gathered = int(gather_results({"best_idx": idx}, world)["best_idx"].shape[0])
+        pf_job = float(np.sum(gather_results({"pf": np.array([info["pair_freq_search"]])}, world)["pf"]))
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -429,14 +449,15 @@ def main():
     line = {
         "metric": "lightcurves/s", "value": value, "unit": "lightcurves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong" if shard is not None else "weak", "vs_baseline": None,
         "dtype": "f32" if args.form == "direct" else args.dtype,
         "data": "synthetic",
         "config": {"workload": name, "form": args.form, "sigma_t": "Bowley-skewness rule",
                    "curves_per_gpu": n, "l2": "flushed between steps (256 MB write)",
                    "tuning": os.path.basename(args.tuning) if tuning is not None else "built-in",
-                   "parallelism": "independent curve batches per GPU"},
-        "pair_freq_per_s": world * pf * args.steps / total_s,
+                   "parallelism": ("one batch split by pair-sum cost across %d GPUs (curve ranges %s)"
+                                   % (world, shard)) if shard is not None else "independent curve batches per GPU"},
+        "pair_freq_per_s": (world * pf if shard is None else pf_job) * args.steps / total_s,
         "gpu_launches": int(info["launches_per_search"]) * args.steps,
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gex2/s",
@@ -453,6 +474,8 @@ def main():
                             "traffic": DRAM_PER_W_BYTE_TENSOR * info["w_bytes_tensor"],
                             "kernel": "k_pair_tensor", "peak_basis": "bf16 dense sustained, " + peaks["source"],
                             "avg_launch_ms": float(info["last_tensor_kernel_ms"])}
+    if shard is not None:
+        line["shard"] = {"ranges": shard, "gathered_curves": gathered}
     if tensor is not None:
         line["tensor"] = tensor
     if transforms is not None:

@@ -4,7 +4,8 @@ Curves are independent (the paper runs one EROS-2 chip per GPU, Section 8),
 so a multi-GPU run gives each rank a contiguous range of curves and needs no
 collective on the data path.  Ranges are balanced by the pair-sum cost of a
 curve, N(N-1)/2 per trial frequency.  The only collectives are the timing
-barrier and the max-over-ranks of elapsed time used for throughput.
+barrier, the max-over-ranks of elapsed time used for throughput, and (after
+the timed work) the gather of each rank's per-curve results in curve order.
 """
 from __future__ import annotations
 
@@ -43,3 +44,17 @@ def max_over_ranks(value: float, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def gather_results(local: dict, world: int) -> dict:
+    """Concatenates every rank's per-curve result arrays (a dict of equal-length
+    numpy arrays for its contiguous curve range) in rank order, which is the
+    global curve order of `curve_ranges`.  Every rank receives the whole
+    result.  Runs over the default process group (any backend); a host-side
+    object gather, not part of the data path."""
+    import torch.distributed as dist
+    if world == 1 or not (dist.is_available() and dist.is_initialized()):
+        return {k: np.asarray(v) for k, v in local.items()}
+    parts = [None] * world
+    dist.all_gather_object(parts, {k: np.asarray(v) for k, v in local.items()})
+    return {k: np.concatenate([p[k] for p in parts]) for k in local}

@@ -7,7 +7,7 @@ import numpy as np
 import torch.multiprocessing as mp
 
 import synth
-from paper_1412_1840_gb300.shard import curve_ranges, local_csr, max_over_ranks
+from paper_1412_1840_gb300.shard import curve_ranges, gather_results, local_csr, max_over_ranks
 
 
 def test_curve_ranges_cover_and_balance():
@@ -67,3 +67,44 @@ def test_two_ranks_shard_and_reduce_time():
     assert res[0][1] == 0 and res[0][2] == res[1][1] and res[1][2] == b.n_curves
     assert res[0][3] + res[1][3] == b.offsets[-1]
     assert res[0][4] == res[1][4] == 2.0        # max over ranks
+
+
+def _oracle_worker(rank, world, port, q):
+    """One rank of a sharded search: the oracle stands in for the GPU on the
+    rank's contiguous curve range; the results are gathered in curve order."""
+    import torch.distributed as dist
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    b = synth.ragged_batch(11, seed=6, n_lo=8, n_hi=40, span=300.0)
+    g = synth.Grid(0.02, 2e-3, 120)
+    a, c = curve_ranges(b.offsets, world)[rank]
+    t, m, e, off = local_csr(b.times, b.mags, b.errs, b.offsets, (a, c))
+    sub = synth.Batch(t, m, e, off, b.period[a:c], b.periodic[a:c], b.kind[a:c])
+    r = oracle.batch_best(sub, g, sigma_t=0.3) if c > a else {
+        "best_idx": np.zeros(0, np.int64), "best_freq": np.zeros(0), "best_stat": np.zeros(0),
+        "is_periodic": np.zeros(0, bool)}
+    got = gather_results({k: r[k] for k in ("best_idx", "best_freq", "best_stat", "is_periodic")}, world)
+    if rank == 0:
+        q.put(got)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_search_gathers_the_whole_batch_result():
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_oracle_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = q.get(timeout=180)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    b = synth.ragged_batch(11, seed=6, n_lo=8, n_hi=40, span=300.0)
+    want = oracle.batch_best(b, synth.Grid(0.02, 2e-3, 120), sigma_t=0.3)
+    for k in ("best_idx", "best_freq", "best_stat", "is_periodic"):
+        np.testing.assert_array_equal(got[k], want[k])
