@@ -16,6 +16,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libcp.so")
+# instruction-rate probes (paper_1412_1840_gb300.peaks): a separate library, not part of the path
+PROBE_SRC = os.path.join(CSRC, "probe", "cp_peaks.cu")
+PROBE_LIB = os.path.join(OUT_DIR, "libcppeaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Host code keeps IEEE evaluation order (no FMA contraction), so FP64 decisions
 # taken on the host match their definitions on any host architecture.
@@ -44,7 +47,30 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def build_probe(force: bool = False) -> str:
+    """Compiles the instruction-rate probes into their own library."""
+    deps = [PROBE_SRC, os.path.join(CSRC, "cp_tc.cuh")]
+    if not force and os.path.exists(PROBE_LIB) and all(os.path.getmtime(d) <= os.path.getmtime(PROBE_LIB) for d in deps):
+        return PROBE_LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = PROBE_LIB + ".tmp%d" % os.getpid()
+    cmd = [nvcc()] + ARCH + FLAGS + ["-shared", "-cudart", "static", PROBE_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for %s:\n%s%s" % (PROBE_SRC, r.stdout, r.stderr))
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    with cf.ThreadPoolExecutor(max_workers=1) as ex:
+        probe = ex.submit(build_probe, force)
+        lib = _build_lib(force, verbose)
+        probe.result()
+    return lib
+
+
+def _build_lib(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
