@@ -34,7 +34,7 @@ PI32 = ctypes.POINTER(ctypes.c_int32)
 class OrcGrid(ctypes.Structure):
     _fields_ = [("f_min", D), ("df", D), ("n_freq", I64), ("hierarchical", ctypes.c_int),
                 ("coarse_df", D), ("top_k", I64), ("fine_df", D), ("fine_halfwidth", D),
-                ("n_bands", I64), ("trials_per_band", I64)]
+                ("n_bands", I64), ("trials_per_band", I64), ("n_exclude", I64), ("exclude", PD)]
 
 
 class OrcOptions(ctypes.Structure):
@@ -82,6 +82,9 @@ def lib():
         L.orc_threshold.restype = D; L.orc_threshold.argtypes = [D]
         L.orc_argmax.restype = I64; L.orc_argmax.argtypes = [PD, I64]
         L.orc_top_local_maxima.restype = I64; L.orc_top_local_maxima.argtypes = [PD, I64, I64, PI64]
+        L.orc_is_excluded.restype = ctypes.c_int; L.orc_is_excluded.argtypes = [D, I64, PD]
+        L.orc_top_local_maxima_excl.restype = I64
+        L.orc_top_local_maxima_excl.argtypes = [PD, I64, I64, D, D, I64, PD, PI64]
         L.orc_curve_best.restype = None
         L.orc_curve_best.argtypes = [PD, PD, PD, I64, I64, ctypes.POINTER(OrcGrid),
                                      ctypes.POINTER(OrcOptions), ctypes.POINTER(OrcResult)]
@@ -309,11 +312,34 @@ def batch_bands_trials(batch, grid) -> np.ndarray:
     return out
 
 
-def _grid(g) -> OrcGrid:
+def _exclude_array(g):
+    ex = np.ascontiguousarray(np.asarray(getattr(g, "exclude", ()) or (), np.float64).reshape(-1))
+    return ex, ex.shape[0] // 2
+
+
+def _grid(g):
+    """(OrcGrid, keepalive) of a synthetic grid description."""
     mode = 2 if getattr(g, "bands", False) else int(bool(g.hierarchical))
-    return OrcGrid(g.f_min, g.df, g.n_freq, mode, g.coarse_df or 0.0,
-                   int(g.top_k or 0), g.fine_df or 0.0, g.fine_halfwidth or 0.0,
-                   int(getattr(g, "n_bands", 0) or 0), int(getattr(g, "trials_per_band", 0) or 0))
+    ex, n_ex = _exclude_array(g)
+    og = OrcGrid(g.f_min, g.df, g.n_freq, mode, g.coarse_df or 0.0,
+                 int(g.top_k or 0), g.fine_df or 0.0, g.fine_halfwidth or 0.0,
+                 int(getattr(g, "n_bands", 0) or 0), int(getattr(g, "trials_per_band", 0) or 0),
+                 n_ex, ex.ctypes.data_as(PD) if n_ex else None)
+    return og, ex
+
+
+def is_excluded(f, exclude) -> bool:
+    """Section 6.1 exclusion test of one frequency against [(lo, hi), ...]."""
+    ex = np.ascontiguousarray(np.asarray(exclude, np.float64).reshape(-1))
+    return bool(lib().orc_is_excluded(float(f), ex.shape[0] // 2, ex.ctypes.data_as(PD) if ex.size else None))
+
+
+def top_local_maxima_excl(v, top_k, f_min, df, exclude) -> np.ndarray:
+    v, pv = _d(v); out = np.zeros(max(int(top_k), 1), dtype=np.int64)
+    ex = np.ascontiguousarray(np.asarray(exclude, np.float64).reshape(-1))
+    n = lib().orc_top_local_maxima_excl(pv, v.shape[0], int(top_k), float(f_min), float(df), ex.shape[0] // 2,
+                                        ex.ctypes.data_as(PD) if ex.size else None, out.ctypes.data_as(PI64))
+    return out[:n]
 
 
 def _opts(sigma_t_mode, sigma_t, per_curve, alpha):
@@ -332,12 +358,12 @@ def batch_best(batch, grid, sigma_t_mode=0, sigma_t=0.3, sigma_t_per_curve=None,
     e = np.ascontiguousarray(batch.errs, np.float32)
     off = np.ascontiguousarray(batch.offsets, np.int64)
     nc = off.shape[0] - 1
-    g = _grid(grid)
+    g, gkeep = _grid(grid)
     o, keep = _opts(sigma_t_mode, sigma_t, sigma_t_per_curve, alpha)
     res = (OrcResult * max(nc, 1))()
     lib().orc_batch_best(t.ctypes.data_as(PD), m.ctypes.data_as(PF), e.ctypes.data_as(PF),
                          off.ctypes.data_as(PI64), nc, ctypes.byref(g), ctypes.byref(o), res)
-    del keep
+    del keep, gkeep
     out = {k: np.array([getattr(res[c], k) for c in range(nc)]) for k, _ in OrcResult._fields_}
     out["best_idx"] = out["best_idx"].astype(np.int64)
     out["is_periodic"] = out["is_periodic"].astype(bool)

@@ -45,6 +45,11 @@
  *     the unweighted Pearson coefficient between the kept magnitudes and the
  *     fitted line; the whole fit a0 + a1 t (intercept included) is removed;
  *     the sample order of the kept points is preserved;
+ *   spurious-period exclusion windows (Section 6.1; the paper's mask widths
+ *     are not given, so the caller supplies closed frequency intervals):
+ *     excluded frequencies are never the best period, nor a coarse peak of the
+ *     coarse-then-fine search; the bands method's trial lists are unchanged
+ *     (the paper filters at the choice of the best trial);
  *   whitening: phase = frac(t / P0); folded order by phase, equal phases by
  *     sample index; the moving average is circular over the folded curve
  *     (the fold is periodic), window of w = min(30, N) samples covering
@@ -251,7 +256,63 @@ typedef struct {
     int64_t top_k;
     double fine_df, fine_halfwidth;
     int64_t n_bands, trials_per_band;   /* bands method (hierarchical == 2) */
+    int64_t n_exclude;                  /* spurious-period exclusion windows, Section 6.1 */
+    const double *exclude;              /* [2 n_exclude]: closed frequency intervals [lo, hi] */
 } orc_grid;
+
+/* Section 6.1: a frequency inside any caller-supplied window [lo, hi]
+ * (closed, 1/day, compared in FP64) is never chosen as the best period; in
+ * the coarse-then-fine search it is not a coarse peak candidate either (its
+ * value still counts in its neighbours' local-maximum tests). */
+int orc_is_excluded(double f, int64_t n_exclude, const double *exclude)
+{
+    for (int64_t q = 0; q < n_exclude; q++)
+        if (f >= exclude[2 * q] && f <= exclude[2 * q + 1])
+            return 1;
+    return 0;
+}
+
+/* Local maxima as in orc_top_local_maxima, excluded frequencies f_min + k df
+ * skipped as candidates (their values stay in the neighbour comparisons). */
+int64_t orc_top_local_maxima_excl(const double *v, int64_t n, int64_t top_k, double f_min, double df,
+                                  int64_t n_exclude, const double *exclude, int64_t *peaks)
+{
+    int64_t cnt = 0;
+    for (int64_t k = 0; k < n; k++) {
+        int left_ok = (k == 0) || (v[k] > v[k - 1]);
+        int right_ok = (k == n - 1) || (v[k] >= v[k + 1]);
+        if (n == 1)
+            left_ok = right_ok = 1;
+        if (!(left_ok && right_ok) || orc_is_excluded(f_min + (double)k * df, n_exclude, exclude))
+            continue;
+        int64_t pos = cnt < top_k ? cnt : top_k;
+        while (pos > 0 && v[k] > v[peaks[pos - 1]])
+            pos--;
+        if (pos >= top_k)
+            continue;
+        int64_t last = cnt < top_k ? cnt : top_k - 1;
+        for (int64_t m = last; m > pos; m--)
+            peaks[m] = peaks[m - 1];
+        peaks[pos] = k;
+        if (cnt < top_k)
+            cnt++;
+    }
+    return cnt;
+}
+
+/* argmax over the entries of v whose frequency fr[k] is not excluded, ties
+ * to the lowest index; -1 when every entry is excluded. */
+static int64_t argmax_allowed(const double *v, const double *fr, int64_t n, const orc_grid *g)
+{
+    int64_t b = -1;
+    for (int64_t k = 0; k < n; k++) {
+        if (orc_is_excluded(fr[k], g->n_exclude, g->exclude))
+            continue;
+        if (b < 0 || v[k] > v[b])
+            b = k;
+    }
+    return b;
+}
 
 typedef struct {
     int sigma_t_mode;               /* 0 fixed, 1 per-curve array, 2 skewness rule */
@@ -295,7 +356,11 @@ static int64_t n_coarse(const orc_grid *g)
  * index rank*(2J+1) + (j+J), which is reported as best_idx.
  * Bands method (hierarchical == 2): the n_bands * trials_per_band trial grid
  * indices of Section 3.1; best over the trial list by value, ties to the
- * lower list position; best_idx is the winning grid index k. */
+ * lower list position; best_idx is the winning grid index k.
+ * Exclusion windows (Section 6.1, orc_is_excluded): excluded frequencies are
+ * skipped by every argmax above (full grid, fine candidates, trial list) and
+ * as coarse peaks; with no admissible candidate best_idx = -1 and the
+ * frequency and statistic are NaN. */
 void orc_curve_best(const double *t, const double *y, const double *e, int64_t n, int64_t c,
                     const orc_grid *g, const orc_options *o, orc_result *r)
 {
@@ -322,8 +387,8 @@ void orc_curve_best(const double *t, const double *y, const double *e, int64_t n
         r->best_idx = -1;
         r->best_freq = NAN;
         r->best_stat = NAN;
-        if (m > 0) {
-            int64_t b = orc_argmax(v, m);
+        int64_t b = argmax_allowed(v, fr, m, g);
+        if (b >= 0) {
             r->best_idx = kk[b];
             r->best_freq = fr[b];
             r->best_stat = v[b];
@@ -338,10 +403,10 @@ void orc_curve_best(const double *t, const double *y, const double *e, int64_t n
         for (int64_t k = 0; k < g->n_freq; k++)
             fr[k] = g->f_min + (double)k * g->df;
         orc_nckp(t, y, n, sy, st, fr, g->n_freq, v);
-        int64_t b = orc_argmax(v, g->n_freq);
+        int64_t b = argmax_allowed(v, fr, g->n_freq, g);
         r->best_idx = b;
-        r->best_freq = fr[b];
-        r->best_stat = v[b];
+        r->best_freq = b >= 0 ? fr[b] : NAN;
+        r->best_stat = b >= 0 ? v[b] : NAN;
         free(fr);
         free(v);
     } else {
@@ -352,7 +417,8 @@ void orc_curve_best(const double *t, const double *y, const double *e, int64_t n
             fr[k] = g->f_min + (double)k * g->coarse_df;
         orc_nckp(t, y, n, sy, st, fr, kc, v);
         int64_t *peaks = (int64_t *)malloc((size_t)(g->top_k > 0 ? g->top_k : 1) * sizeof(int64_t));
-        int64_t np = orc_top_local_maxima(v, kc, g->top_k, peaks);
+        int64_t np = orc_top_local_maxima_excl(v, kc, g->top_k, g->f_min, g->coarse_df, g->n_exclude, g->exclude,
+                                               peaks);
         int64_t J = (int64_t)floor(g->fine_halfwidth / g->fine_df + 0.5);
         int64_t w = 2 * J + 1;
         double best = -INFINITY, bestf = fr[0];
@@ -366,7 +432,7 @@ void orc_curve_best(const double *t, const double *y, const double *e, int64_t n
             int64_t *jl = w <= 4096 ? jj : (int64_t *)malloc((size_t)w * sizeof(int64_t));
             for (int64_t j = -J; j <= J; j++) {
                 double f = fp + (double)j * g->fine_df;
-                if (f < g->f_min || f > f_max)
+                if (f < g->f_min || f > f_max || orc_is_excluded(f, g->n_exclude, g->exclude))
                     continue;
                 ff[m] = f;
                 jl[m] = j;
@@ -385,15 +451,15 @@ void orc_curve_best(const double *t, const double *y, const double *e, int64_t n
                 free(jl);
         }
         r->best_idx = bestc;
-        r->best_freq = bestf;
-        r->best_stat = best;
+        r->best_freq = bestc >= 0 ? bestf : NAN;
+        r->best_stat = bestc >= 0 ? best : NAN;
         free(ff);
         free(fv);
         free(peaks);
         free(fr);
         free(v);
     }
-    r->is_periodic = r->best_stat > orc_threshold(r->psnr);
+    r->is_periodic = r->best_stat > orc_threshold(r->psnr);   /* false when no candidate (NaN) */
 }
 
 /* Batch driver over a CSR lightcurve set (times f64, mags/errs f32 as

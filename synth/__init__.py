@@ -82,6 +82,7 @@ class Grid:
     bands: bool = False
     n_bands: int = 0
     trials_per_band: int = 0
+    exclude: tuple = ()          # spurious-period exclusion windows: ((f_lo, f_hi), ...) in 1/day
 
     @property
     def f_max(self) -> float:

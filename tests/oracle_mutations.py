@@ -59,9 +59,16 @@ core = [
  ("sigma_y: largest error bar", "    double sy = orc_median(e, n);\n    double st = curve_sigma_t(o, y, n, c);",
   "    double sy = orc_quantile(e, n, 1.0);\n    double st = curve_sigma_t(o, y, n, c);"),
  ("discriminator: flipped", "r->is_periodic = r->best_stat > orc_threshold(r->psnr);", "r->is_periodic = r->best_stat < orc_threshold(r->psnr);"),
+ ("exclusion: open intervals", "if (f >= exclude[2 * q] && f <= exclude[2 * q + 1])", "if (f > exclude[2 * q] && f < exclude[2 * q + 1])"),
+ ("exclusion: coarse peaks unfiltered", "if (!(left_ok && right_ok) || orc_is_excluded(f_min + (double)k * df, n_exclude, exclude))",
+  "if (!(left_ok && right_ok))"),
+ ("exclusion: fine candidates unfiltered", "if (f < g->f_min || f > f_max || orc_is_excluded(f, g->n_exclude, g->exclude))",
+  "if (f < g->f_min || f > f_max)"),
+ ("exclusion: trial choice unfiltered", "int64_t b = argmax_allowed(v, fr, m, g);", "int64_t b = m > 0 ? orc_argmax(v, m) : -1;"),
+ ("exclusion: full-grid choice unfiltered", "int64_t b = argmax_allowed(v, fr, g->n_freq, g);", "int64_t b = orc_argmax(v, g->n_freq);"),
 ]
 tests = ["tests/test_oracle_bands.py", "tests/test_oracle_prep.py", "tests/test_oracle_whiten.py"]
-core_tests = ["tests/test_oracle_pins.py"]
+core_tests = ["tests/test_oracle_pins.py", "tests/test_oracle_exclusion.py"]
 results = []
 only = sys.argv[1:]            # optional name prefixes: run just those mutations
 for name, old, new, tfiles in [m + (core_tests,) for m in core] + [m + (tests,) for m in muts]:
