@@ -267,13 +267,19 @@ __global__ void __launch_bounds__(256) k_build_w(const BuildWArgs a)
 // k_pair_direct: persistent CTAs pop (curve, frequency-chunk) units.
 // ===========================================================================
 constexpr int kPairThreads = 512;
-constexpr int kHalfRows = kRowsPerLane / 2;   // rows per lane in a half-tile work item
+// Rows per lane in one warp work item: 8 = a whole 32 x 32 tile (each lane 8
+// rows x 4 columns), 4 = half a tile.  Every trig value a lane loads from
+// shared memory serves (rows x columns) / (rows + columns) evaluations, so the
+// whole-tile item needs a third fewer shared-memory loads per evaluation.
+constexpr int kItemRows = 8;
+constexpr int kItemsPerTile = kRowsPerLane / kItemRows;
+constexpr bool kPrefetchW = kItemRows == 4;   // next item's W in registers (the half-tile item only)
 // Curves with sigma_t at or above this take the exponent in the cos form (see
 // pair_item); below it the sin form keeps the exponent's rounding relative.
 constexpr float kCosFormMinSigma = 0.3f;
 
-// One work item (16 rows x 32 columns of a tile) at every frequency pair of
-// the unit.  The exponent of the periodic kernel (Eq. (periodickernel)),
+// One work item (4 kItemRows rows x 32 columns of a tile) at every frequency
+// pair of the unit.  The exponent of the periodic kernel (Eq. (periodickernel)),
 // -beta sin^2(pi dphi) with beta = 2 log2(e) / sigma_t^2, is taken in one of
 // two forms from the trig table of the unit:
 //   sin form  -(c_i s_j - s_i c_j)^2 with (s, c) = (sin, cos)(pi phi) sqrt(beta)
@@ -284,8 +290,8 @@ constexpr float kCosFormMinSigma = 0.3f;
 // is used only for sigma_t >= kCosFormMinSigma (beta <= 32: below 3e-6 per term).
 template <bool COSF>
 __device__ __forceinline__ void pair_item(const ulonglong2* SC, const f2* NS, int npad, int nfp, int rbase,
-                                          int cbase, f2 nhalf, const f2 (&w01)[kHalfRows],
-                                          const f2 (&w23)[kHalfRows], f2 (&acc)[kFcMax / 2])
+                                          int cbase, f2 nhalf, const f2 (&w01)[kItemRows],
+                                          const f2 (&w23)[kItemRows], f2 (&acc)[kFcMax / 2])
 {
 #pragma unroll
     for (int fp = 0; fp < kFcMax / 2; fp++) {
@@ -297,7 +303,7 @@ __device__ __forceinline__ void pair_item(const ulonglong2* SC, const f2* NS, in
             for (int m = 0; m < kColsPerLane; m++) col[m] = SCf[cbase + 8 * m];
             f2 tf0 = 0ull, tf1 = 0ull, tg0 = 0ull, tg1 = 0ull;
 #pragma unroll
-            for (int k = 0; k < kHalfRows; k++) {
+            for (int k = 0; k < kItemRows; k++) {
                 const int i = rbase + 4 * k;
                 float e[kColsPerLane][2];
                 if (COSF) {
@@ -433,38 +439,40 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
 
         const int nb = npad / kTile;
         const int ntiles = nb * (nb + 1) / 2;
-        const int nitems = 2 * ntiles;           // (tile, row half): 16 x 32 pairs per warp item
+        const int nitems = kItemsPerTile * ntiles;   // (tile, row part): 4 kItemRows x 32 pairs per warp item
         const float4* Wc = reinterpret_cast<const float4*>(a.W + (a.wtile_start[slot] - a.wtile_base) * kTileFloats);
         f2 acc[kFcMax / 2];                      // per f-pair: (sum at f, sum at f')
         const f2 nhalf = pk(-ts * ts, -ts * ts);   // cos form: -beta/2
 #pragma unroll
         for (int q = 0; q < kFcMax / 2; q++) acc[q] = 0ull;
 
-        // W of the first item; each item prefetches the next one's
-        float4 wn[kHalfRows];
+        // W of an item: rows (item % kItemsPerTile) * kItemRows + k of the stored tile
+        auto w_ptr = [&](int it, int k) {
+            return Wc + (int64_t)(it / kItemsPerTile) * (kTileFloats / 4) + ((it % kItemsPerTile) * kItemRows + k) * 32 + lane;
+        };
+        float4 wn[kPrefetchW ? kItemRows : 1];
         int item = warp;
-        if (item < nitems) {
+        if (kPrefetchW && item < nitems) {
 #pragma unroll
-            for (int k = 0; k < kHalfRows; k++)
-                wn[k] = __ldg(Wc + (int64_t)(item >> 1) * (kTileFloats / 4) + ((item & 1) * kHalfRows + k) * 32 + lane);
+            for (int k = 0; k < kItemRows; k++) wn[k] = __ldg(w_ptr(item, k));
         }
 #pragma unroll 1
         for (; item < nitems; item += NW) {
-            f2 w01[kHalfRows], w23[kHalfRows];
+            f2 w01[kItemRows], w23[kItemRows];
 #pragma unroll
-            for (int k = 0; k < kHalfRows; k++) {
-                w01[k] = pk(wn[k].x, wn[k].y);
-                w23[k] = pk(wn[k].z, wn[k].w);
+            for (int k = 0; k < kItemRows; k++) {
+                const float4 wv = kPrefetchW ? wn[k] : __ldg(w_ptr(item, k));
+                w01[k] = pk(wv.x, wv.y);
+                w23[k] = pk(wv.z, wv.w);
             }
             const int nxt = item + NW;
-            if (nxt < nitems) {
+            if (kPrefetchW && nxt < nitems) {
 #pragma unroll
-                for (int k = 0; k < kHalfRows; k++)
-                    wn[k] = __ldg(Wc + (int64_t)(nxt >> 1) * (kTileFloats / 4) + ((nxt & 1) * kHalfRows + k) * 32 + lane);
+                for (int k = 0; k < kItemRows; k++) wn[k] = __ldg(w_ptr(nxt, k));
             }
             int bi, bj;
-            decode_tile(item >> 1, nb, bi, bj);
-            const int rbase = bi * kTile + (item & 1) * (kTile / 2) + la;
+            decode_tile(item / kItemsPerTile, nb, bi, bj);
+            const int rbase = bi * kTile + (item % kItemsPerTile) * (4 * kItemRows) + la;
             const int cbase = bj * kTile + lb;
             if (cosf) pair_item<true>(SC, NS, npad, nfp, rbase, cbase, nhalf, w01, w23, acc);
             else pair_item<false>(SC, NS, npad, nfp, rbase, cbase, nhalf, w01, w23, acc);
@@ -498,17 +506,17 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
                 const long long kk = kfirst + lane;
                 if (a.stage == kStageFull) {
                     if (a.out) a.out[(int64_t)c * a.out_ld + kk] = v;
-                    key = make_key(v, (uint32_t)kk);
+                    if (!excluded_k(a.ex.full_k, a.ex.n, kk)) key = make_key(v, (uint32_t)kk);
                 } else if (a.stage == kStageCoarse) {
                     a.coarse_out[(int64_t)c * a.n_freq + kk] = v;
                 } else if (a.stage == kStageList) {
                     const bool valid = tl[kk] >= 0;
                     if (a.trial_stat) a.trial_stat[(int64_t)c * a.n_trials + kk] = valid ? v : __int_as_float(0x7fc00000);
-                    if (valid) key = make_key(v, (uint32_t)kk);
+                    if (valid && !excluded_k(a.ex.full_k, a.ex.n, tl[kk])) key = make_key(v, (uint32_t)kk);
                 } else {
-                    const double fpk = a.f_min + (double)peak_mult * a.coarse_df;
-                    const double f = fpk + (double)kk * a.step;
-                    if (f >= a.f_min && f <= a.f_max)
+                    const double fpk = grid_freq(a.f_min, (double)peak_mult, a.coarse_df);
+                    const double f = grid_freq(fpk, (double)kk, a.step);
+                    if (f >= a.f_min && f <= a.f_max && !excluded_f(a.ex, f))
                         key = make_key(v, (uint32_t)(peak * (2 * a.fine_half + 1) + (kk + a.fine_half)));
                 }
             }
@@ -546,7 +554,7 @@ __global__ void __launch_bounds__(256) k_topk(const TopkArgs a)
             const float x = v[k];
             const bool lok = (k == 0) || (x > v[k - 1]);
             const bool rok = (k == K - 1) || (x >= v[k + 1]);
-            if (lok && rok) {
+            if (lok && rok && !excluded_k(a.ex.coarse_k, a.ex.n, k)) {
                 const unsigned long long key = make_key(x, (uint32_t)k);
                 if (key < prev && key > best) best = key;
             }
