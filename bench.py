@@ -40,7 +40,15 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-MUFU_EX2_PER_CLK_SM = 32      # measured sm_103a SFU ex2 rate (ex2 probe, 152 SMs)
+PEAKS_TABLE = os.path.join(ROOT, "paper_1412_1840_gb300", "peaks_gb300.json")
+SM_MAX_MHZ = 2070.0
+
+
+def sfu_ex2_per_clk_sm():
+    """MUFU ex2.approx.f32 per clock per SM measured on this GPU by the
+    package's instruction-rate probes (paper_1412_1840_gb300.peaks)."""
+    with open(PEAKS_TABLE) as f:
+        return float(json.load(f)["rates"]["ex2_f32"]["per_clk_per_sm"])
 # DRAM bytes per byte of period-independent magnitude-kernel tiles, measured with
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) on 256 curves x 2,048
 # frequencies: each tile is read from DRAM once per search, later units of the
@@ -78,6 +86,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-transforms", action="store_true", help="skip timing preprocessing and whitening")
+    ap.add_argument("--no-hierarchical", action="store_true",
+                    help="skip the coarse-then-fine search on the same batch (both forms)")
+    ap.add_argument("--no-throughput", action="store_true",
+                    help="skip the 200,000-curve two-band throughput run (both forms, one timed step each)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--shard", action="store_true",
                     help="under torchrun: split ONE batch across the ranks by pair-sum cost (strong scaling) "
@@ -359,9 +371,9 @@ def main():
                         device=local, stream=stream.cuda_stream, **tkw2)
         tidx = np.empty(n, np.int64); tbf = np.empty(n, np.float64); tbs = np.empty(n, np.float32)
         tper = np.empty(n, np.uint8); tps = np.empty(n, np.float32)
-        for _ in range(max(1, min(args.warmup, 2))):
+        for _ in range(max(1, min(args.warmup, 3))):
             tplan.best_period_into(tidx, tbf, tbs, tper, tps)
-        t_steps = max(1, min(args.steps, 2))
+        t_steps = args.steps                   # the same timed steps as the direct form
         te0 = [torch.cuda.Event(enable_timing=True) for _ in range(t_steps)]
         te1 = [torch.cuda.Event(enable_timing=True) for _ in range(t_steps)]
         tk_ms = []
@@ -388,6 +400,7 @@ def main():
             "class_curves": dict(zip(["direct", "n4", "n8", "n12", "n16", "n32"], ti["class_curves"])),
             "best_idx_agreement_vs_direct": float(np.mean(tidx == idx)),
             "best_stat_max_rel_diff_vs_direct": float(rel.max()),
+            "within_1e-3_of_direct": bool(rel.max() <= 1e-3),
             "clocks": tclk.summary(),
             "roofline": {"bound": "tensor", "achieved": tflops,
                          "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
@@ -405,32 +418,138 @@ def main():
             thplan.best_period_into(tidx, tbf, tbs, tper, tps)
             barrier()
             t0 = time.perf_counter()
-            for _ in range(t_steps):
+            te_steps = max(1, min(args.steps, 3))
+            for _ in range(te_steps):
                 thplan.best_period_into(tidx, tbf, tbs, tper, tps)
             barrier()
             te_s = max_over_ranks(time.perf_counter() - t0, device=dev)
             thplan.close()
-            tensor["e2e"] = {"value": n_job * t_steps / te_s, "unit": "lightcurves/s",
-                             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": t_steps}
-        # the other 16-bit operand type on the same batch (same plan shape, one timed step)
+            tensor["e2e"] = {"value": n_job * te_steps / te_s, "unit": "lightcurves/s",
+                             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": te_steps}
+        # the other 16-bit operand type on the same batch (same plan shape, a few timed steps)
         other = cp.CP_DTYPE_FP16 if args.dtype == "bf16" else cp.CP_DTYPE_BF16
         oplan = cp.Plan(td, md, ed, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=cp.CP_FORM_TENSOR,
                         device=local, stream=stream.cuda_stream, n_max=args.n_max, dtype=other, tuning=tuning)
         oplan.best_period_into(tidx, tbf, tbs, tper, tps)
+        o_steps = max(1, min(args.steps, 3))
         barrier()
-        oe0, oe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.fill_(7)
-        oe0.record(stream)
-        oplan.best_period_into(tidx, tbf, tbs, tper, tps)
-        oe1.record(stream)
-        barrier()
-        o_s = max_over_ranks(oe0.elapsed_time(oe1) / 1e3, device=dev)
+        o_ms = []
+        for k in range(o_steps):
+            oe0, oe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(7 + k)
+            oe0.record(stream)
+            oplan.best_period_into(tidx, tbf, tbs, tper, tps)
+            oe1.record(stream)
+            barrier()
+            o_ms.append(oe0.elapsed_time(oe1))
+        oi = oplan.info()
+        o_s = max_over_ranks(sum(o_ms) / 1e3, device=dev)
         oplan.close()
         orel = np.abs(tbs.astype(np.float64) - bs) / np.maximum(np.abs(bs.astype(np.float64)), 1e-30)
+        otf = oi["tensor_flops_search"] / (oi["last_tensor_kernel_ms"] / 1e3) / 1e12
         tensor["other_dtype"] = {"dtype": "fp16" if other == cp.CP_DTYPE_FP16 else "bf16",
-                                 "value": n_job / o_s, "unit": "lightcurves/s", "ms_per_step": o_s * 1e3,
+                                 "value": n_job * o_steps / o_s, "unit": "lightcurves/s",
+                                 "ms_per_step": o_s * 1e3 / o_steps, "steps": o_steps,
                                  "best_idx_agreement_vs_direct": float(np.mean(tidx == idx)),
-                                 "best_stat_max_rel_diff_vs_direct": float(orel.max())}
+                                 "best_stat_max_rel_diff_vs_direct": float(orel.max()),
+                                 "within_1e-3_of_direct": bool(orel.max() <= 1e-3),
+                                 "operands": "W' as hi + lo BF16 parts (two MMAs per K slice), Z one BF16 part"
+                                 if other == cp.CP_DTYPE_BF16 else "FP16",
+                                 "tensor_tflops_algorithmic": otf}
+
+    # ---- coarse-then-fine search on the same batch (both forms) -------------
+    hier = None
+    if not args.no_hierarchical and args.workload == "ragged" and shard is None:
+        hb, hg = synth.workload_hierarchical(n, args.seed + 1000 * rank)
+        assert np.array_equal(hb.offsets, b.offsets) and np.array_equal(hb.mags, b.mags)   # the same batch
+        hgrid = cp.grid_from(hg)
+        hidx = np.empty(n, np.int64); hbf = np.empty(n, np.float64); hbs = np.empty(n, np.float32)
+        hper = np.empty(n, np.uint8); hps = np.empty(n, np.float32)
+        hier = {"workload": "%d curves N~U[300,1000] seasonal 2500 d; coarse 0.002-5 step 1e-3 (4,999), top-10 "
+                            "refined at 1e-5 over +-2e-3 (401 each)" % n}
+        for fname, fkw in (("direct", dict(form=cp.CP_FORM_DIRECT)),
+                           ("tensor", dict(form=cp.CP_FORM_TENSOR, n_max=args.n_max, dtype=cp.CP_DTYPE_FP16))):
+            hp = cp.Plan(td, md, ed, hb.offsets, hgrid, sigma_t_mode=cp.CP_SIGMA_T_RULE, device=local,
+                         stream=stream.cuda_stream, tuning=tuning, **fkw)
+            hp.best_period_into(hidx, hbf, hbs, hper, hps)
+            h_steps = max(1, min(args.steps, 5))
+            ms, km = [], []
+            barrier()
+            for k in range(h_steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(k & 0xff)
+                e0.record(stream)
+                hp.best_period_into(hidx, hbf, hbs, hper, hps)
+                e1.record(stream)
+                barrier()
+                ms.append(e0.elapsed_time(e1))
+                hi_ = hp.info()
+                km.append(hi_["last_tensor_kernel_ms"] if fname == "tensor" else hi_["last_pair_kernel_ms"])
+            hp.close()
+            h_s = max_over_ranks(sum(ms) / 1e3, device=dev)
+            ent = {"value": n * h_steps / h_s, "unit": "lightcurves/s", "steps": h_steps,
+                   "ms_per_step": h_s * 1e3 / h_steps, "pair_freq_per_s": hi_["pair_freq_search"] * h_steps / h_s,
+                   "launches_per_search": int(hi_["launches_per_search"])}
+            if fname == "tensor":
+                ent["roofline_frac"] = hi_["tensor_flops_search"] / (np.mean(km) / 1e3) / 1e12 / \
+                    measured_peaks()["bf16_tflops_sustained"]
+                ent["dtype"] = "fp16"
+            else:
+                ent["roofline_frac"] = hi_["pair_freq_search"] / (np.mean(km) / 1e3) / \
+                    (sfu_ex2_per_clk_sm() * hi_["n_sm"] * SM_MAX_MHZ * 1e6)
+            hier[fname] = ent
+
+    # ---- the 200,000-curve two-band throughput run (both forms) -----------
+    thr = None
+    if not args.no_throughput and args.workload == "ragged" and shard is None and world == 1:
+        del td, md, ed
+        torch.cuda.empty_cache()
+        t_gen = time.perf_counter()
+        tb, tg = synth.workload_throughput(100000, 5)
+        t_gen = time.perf_counter() - t_gen
+        ttd = torch.from_numpy(tb.times).to(dev)
+        tmd = torch.from_numpy(tb.mags).to(dev)
+        ted = torch.from_numpy(tb.errs).to(dev)
+        tn = tb.n_curves
+        ti_ = np.empty(tn, np.int64); tf_ = np.empty(tn, np.float64); ts_ = np.empty(tn, np.float32)
+        tp_ = np.empty(tn, np.uint8); tq_ = np.empty(tn, np.float32)
+        thr = {"workload": "100,000 two-band sources (200,000 curves) N~U[200,1000] per band, SNR 0.2-10, seed 5; "
+                           "coarse 0.002-5 step 1e-3, top-10 refined at 1e-5 over +-2e-3",
+               "generator_s": t_gen}
+        res = {}
+        for fname, fkw, warm in (("tensor", dict(form=cp.CP_FORM_TENSOR, n_max=args.n_max, dtype=cp.CP_DTYPE_FP16), 1),
+                                 ("direct", dict(form=cp.CP_FORM_DIRECT), 0)):
+            tpl = cp.Plan(ttd, tmd, ted, tb.offsets, cp.grid_from(tg), sigma_t_mode=cp.CP_SIGMA_T_RULE,
+                          device=local, stream=stream.cuda_stream, tuning=tuning, **fkw)
+            for _ in range(warm):
+                tpl.best_period_into(ti_, tf_, ts_, tp_, tq_)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tpl.best_period_into(ti_, tf_, ts_, tp_, tq_)
+            e1.record(stream)
+            barrier()
+            t_ms = e0.elapsed_time(e1)
+            tinfo = tpl.info()
+            tpl.close()
+            res[fname] = ts_.copy()
+            ent = {"value": tn / (t_ms / 1e3), "unit": "lightcurves/s", "steps": 1, "warmup": warm,
+                   "ms_per_step": t_ms, "pair_freq_per_s": tinfo["pair_freq_search"] / (t_ms / 1e3)}
+            if fname == "tensor":
+                ent["dtype"] = "fp16"
+                ent["roofline_frac"] = tinfo["tensor_flops_search"] / (tinfo["last_tensor_kernel_ms"] / 1e3) / 1e12 / \
+                    measured_peaks()["bf16_tflops_sustained"]
+            else:
+                ent["note"] = "no warm-up step (kernels already loaded by the runs above; the first call " \
+                              "instantiates its CUDA graph inside the timed step)"
+                ent["roofline_frac"] = tinfo["pair_freq_search"] / (tinfo["last_pair_kernel_ms"] / 1e3) / \
+                    (sfu_ex2_per_clk_sm() * tinfo["n_sm"] * SM_MAX_MHZ * 1e6)
+            thr[fname] = ent
+        rel = np.abs(res["tensor"].astype(np.float64) - res["direct"]) / \
+            np.maximum(np.abs(res["direct"].astype(np.float64)), 1e-30)
+        thr["tensor_best_stat_max_rel_diff_vs_direct"] = float(rel.max())
+        thr["agreement_with_oracle"] = "tests/test_gpu_agreement.py: fixed 1,000-curve sample of this generator"
+        del ttd, tmd, ted
 
     gathered = None
     if shard is not None:
@@ -445,7 +564,8 @@ def main():
     pf = info["pair_freq_search"]
     pair_s = np.mean(pair_ms) / 1e3
     achieved = pf / pair_s / 1e9                       # Gex2/s: one ex2 per pair-frequency evaluation
-    peak = MUFU_EX2_PER_CLK_SM * info["n_sm"] * 2070e6 / 1e9
+    ex2_clk = sfu_ex2_per_clk_sm()
+    peak = ex2_clk * info["n_sm"] * SM_MAX_MHZ * 1e6 / 1e9
     line = {
         "metric": "lightcurves/s", "value": value, "unit": "lightcurves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
@@ -462,8 +582,10 @@ def main():
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gex2/s",
                      "frac": achieved / peak, "traffic": DRAM_PER_W_BYTE_DIRECT * info["w_bytes_direct"],
-                     "kernel": "k_pair_direct", "peak_basis": "32 MUFU ex2/clk/SM x %d SMs x 2070 MHz (max SM clock)"
-                     % info["n_sm"], "avg_launch_ms": float(np.mean(pair_ms))},
+                     "kernel": "k_pair_direct",
+                     "peak_basis": "%.2f MUFU ex2/clk/SM (measured by paper_1412_1840_gb300.peaks on GB300) x %d SMs "
+                                   "x %.0f MHz (max SM clock)" % (ex2_clk, info["n_sm"], SM_MAX_MHZ),
+                     "avg_launch_ms": float(np.mean(pair_ms))},
         "clocks": clocks,
     }
     if args.form == "tensor":
@@ -478,6 +600,10 @@ def main():
         line["shard"] = {"ranges": shard, "gathered_curves": gathered}
     if tensor is not None:
         line["tensor"] = tensor
+    if hier is not None:
+        line["hierarchical"] = hier
+    if thr is not None:
+        line["throughput"] = thr
     if transforms is not None:
         line["transforms"] = transforms
     if getattr(g, "bands", False):

@@ -19,9 +19,12 @@
  * pSNR = 0.7413 iqr(y) / (alpha med(e)) (Eq. (pSNR), Section 5.2).
  *
  * All entry points return a cp_status and never throw.  On failure
- * cp_last_error() returns a thread-local message.  Nothing is computed on
- * the CPU: every step of the method runs in CUDA kernels on the plan's
- * device; a missing or unusable device is an error (CP_ECUDA).
+ * cp_last_error() returns a thread-local message.  Every step of the method
+ * runs in CUDA kernels on the plan's device; the host validates arguments,
+ * schedules work units and launches (its one piece of arithmetic is the
+ * table of sigma_t thresholds that picks the tensor form's harmonic count,
+ * from the FP64 coefficients of cp_bessel_coefficients).  A missing or
+ * unusable device is an error (CP_ECUDA).
  */
 #ifndef CP_H
 #define CP_H
@@ -84,13 +87,34 @@ enum { CP_MEM_HOST = 0, CP_MEM_DEVICE = 1 };
  *   6. the trials_per_band highest local maxima of S_b (local maximum and
  *      tie rule as above), leaving out the one-day frequencies
  *      |1/f - 1| < 1e-4 (FP64).
+ * The window is evaluated in FP32 over the grid; every local-maximum test
+ * and every ordering that lies within the FP32 error bound is decided again
+ * from FP64 window values (exact 64-bit phases), and a band whose candidate
+ * set the bound cannot prove complete is scanned in FP64 over the whole grid,
+ * so the lists are those of an FP64 evaluation (n_freq < 2^29).
  * nCKP is then evaluated at the n_bands * trials_per_band trial grid
  * frequencies only, and the best is the largest, ties to the lower
  * position in the band-major trial list.  best_idx is the winning grid
  * index k.  cp_trial_frequencies returns the list and its nCKP values.
+ *
+ * Spurious-period exclusion windows (Section 6.1, Filtering of spurious
+ * periods; Table tab:spuriousperiods lists the periods -- the solar day, the
+ * synodic month, the year, the time span and their aliases -- but not the
+ * widths of the paper's masks, so the caller supplies them): n_exclude closed
+ * frequency intervals exclude[2q] <= f <= exclude[2q+1] (1/day).  A frequency
+ * f in any window (compared in FP64 with f computed as for best_freq) is
+ * never returned as the best: the full-grid argmax and the choice among
+ * the refined candidates and among the bands trials skip it, and the
+ * coarse-then-fine search does not take it as a coarse peak (its value
+ * still counts in its neighbours' local-maximum tests).  The bands trial
+ * lists themselves are unchanged (the paper filters at the choice of the
+ * best trial).  cp_periodogram is unaffected.  A curve left without any
+ * admissible candidate reports best_idx -1, NaN frequency and statistic,
+ * and is_periodic 0.
  */
 enum { CP_SEARCH_FULL = 0, CP_SEARCH_COARSE_FINE = 1, CP_SEARCH_BANDS = 2 };
 #define CP_BANDS_MAX_TRIALS 512
+#define CP_MAX_EXCLUDE 64
 
 typedef struct {
     double f_min;
@@ -103,6 +127,10 @@ typedef struct {
     double fine_halfwidth;
     int32_t n_bands;                 /* bands method: N_b in [1, 10]                   */
     int32_t trials_per_band;         /* bands method: N_t in [1, CP_BANDS_MAX_TRIALS]  */
+    int32_t n_exclude;               /* exclusion windows: 0..CP_MAX_EXCLUDE           */
+    int32_t reserved0;
+    const double *exclude;           /* host, 2 n_exclude values: [lo, hi] pairs with  */
+                                     /* finite lo <= hi (1/day); copied by cp_plan     */
 } cp_freq_grid;
 
 /*
@@ -138,8 +166,14 @@ typedef struct {
     int32_t n_max;                   /* harmonics of the tensor form (4, 8, 12, 16, 32); */
                                      /* 0 = per curve: the smallest of 8, 12, 16, 32 whose */
                                      /* truncation tail is <= 1e-4 of the kernel peak   */
-                                     /* for the curve's sigma_t at plan time; curves    */
-                                     /* that need more run in the direct form           */
+                                     /* for the curve's sigma_t (computed on the device */
+                                     /* at plan time); curves that need more run in the */
+                                     /* direct form.  Each call checks, on the device,  */
+                                     /* that every curve's current sigma_t is still     */
+                                     /* covered by its count; if one is not (the        */
+                                     /* magnitudes changed, e.g. by cp_whiten), the     */
+                                     /* call rebuilds the plan on the new sigma_t and   */
+                                     /* runs again (cp_plan_info.replans counts this)   */
     int32_t input_memory;            /* CP_MEM_HOST or CP_MEM_DEVICE                    */
     int32_t use_graph;               /* capture cp_best_period's step in a CUDA graph   */
     int32_t device;                  /* CUDA device ordinal                             */
@@ -196,13 +230,18 @@ cp_status cp_periodogram(cp_plan_t plan, float *out);
  *   best_stat  nCKP at the best frequency
  *   is_periodic  1 if best_stat > th(pSNR bin) of Table tab:th
  *   psnr       pSNR of Eq. (pSNR)
- * Synchronous: returns after the results are on the host.
+ * Synchronous: returns after the results are on the host.  With per-curve
+ * harmonic counts (tensor form, n_max = 0) a call may rebuild the plan first
+ * (see cp_options.n_max); the results are then those of the rebuilt plan.
  */
 cp_status cp_best_period(cp_plan_t plan, int64_t *best_idx, double *best_freq, float *best_stat,
                          uint8_t *is_periodic, float *psnr);
 
 /* Waits for the plan's stream and returns the device-side status of the
- * last call (CP_EINVAL for non-finite inputs or a zero median error). */
+ * last call (CP_EINVAL for non-finite inputs or a zero median error).  If the
+ * last call was a cp_periodogram whose per-curve harmonic counts no longer
+ * cover a curve's sigma_t, it rebuilds the plan and runs that pass again
+ * into the same output before returning. */
 cp_status cp_sync(cp_plan_t plan);
 
 /*
@@ -290,6 +329,12 @@ typedef struct {
                                   /* grid frequency) of one cp_best_period              */
     double w_bytes_direct;        /* bytes of the magnitude-kernel tiles one search     */
     double w_bytes_tensor;        /* builds for the direct / tensor-form curves         */
+    int64_t replans;              /* plans rebuilt after a curve's sigma_t left the     */
+                                  /* range of its harmonic count (see cp_options.n_max) */
+    int64_t bands_exact_scans;    /* bands method, last search: (curve, band) lists     */
+                                  /* chosen by a whole-grid FP64 scan because the FP32  */
+                                  /* window bound could not prove the candidate set     */
+                                  /* complete (peaks of nearly equal height)            */
 } cp_plan_info;
 
 cp_status cp_get_plan_info(cp_plan_t plan, cp_plan_info *info);
@@ -327,7 +372,8 @@ cp_status cp_bessel_coefficients(double sigma_t, int32_t n_max, double *out);
  *   offsets             HOST int64, n_curves+1 entries, offsets[0] = 0.
  *   n_curves            1 .. CP_NOALLOC_MAX_CURVES; the whole batch must fit
  *                       the scratch array (CP_EUNSUPPORTED otherwise).
- *   grid                as in cp_plan (full or coarse-then-fine).
+ *   grid                as in cp_plan (full or coarse-then-fine, no exclusion
+ *                       windows: CP_EUNSUPPORTED otherwise).
  *   sigma_t             fixed periodic-kernel size, > 0.
  *   cuda_stream         stream of the current device (NULL = legacy default).
  *   best_idx, best_freq, best_stat, is_periodic

@@ -29,6 +29,7 @@ CP_SIGMA_T_FIXED, CP_SIGMA_T_PER_CURVE, CP_SIGMA_T_RULE = 0, 1, 2
 CP_MEM_HOST, CP_MEM_DEVICE = 0, 1
 CP_SEARCH_FULL, CP_SEARCH_COARSE_FINE, CP_SEARCH_BANDS = 0, 1, 2
 CP_BANDS_MAX_TRIALS = 512
+CP_MAX_EXCLUDE = 64
 
 
 class CpError(RuntimeError):
@@ -41,7 +42,9 @@ class cp_freq_grid(ctypes.Structure):
     _fields_ = [("f_min", ctypes.c_double), ("df", ctypes.c_double), ("n_freq", ctypes.c_int64),
                 ("hierarchical", ctypes.c_int32), ("top_k", ctypes.c_int32), ("coarse_df", ctypes.c_double),
                 ("fine_df", ctypes.c_double), ("fine_halfwidth", ctypes.c_double),
-                ("n_bands", ctypes.c_int32), ("trials_per_band", ctypes.c_int32)]
+                ("n_bands", ctypes.c_int32), ("trials_per_band", ctypes.c_int32),
+                ("n_exclude", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("exclude", ctypes.POINTER(ctypes.c_double))]
 
 
 CP_TUNE_MAX_BUCKETS = 16
@@ -88,7 +91,8 @@ class cp_plan_info(ctypes.Structure):
                 ("tensor_flops_search", ctypes.c_double), ("direct_pair_freq_search", ctypes.c_double),
                 ("last_bands_kernel_ms", ctypes.c_float), ("reserved0", ctypes.c_float),
                 ("window_terms_search", ctypes.c_double), ("w_bytes_direct", ctypes.c_double),
-                ("w_bytes_tensor", ctypes.c_double)]
+                ("w_bytes_tensor", ctypes.c_double), ("replans", ctypes.c_int64),
+                ("bands_exact_scans", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -182,12 +186,19 @@ def cp_bessel_coefficients(sigma_t: float, n_max: int) -> np.ndarray:
 
 
 def make_grid(f_min, df, n_freq, hierarchical=False, coarse_df=0.0, top_k=0, fine_df=0.0, fine_halfwidth=0.0,
-              bands=False, n_bands=0, trials_per_band=0):
+              bands=False, n_bands=0, trials_per_band=0, exclude=()):
     """cp_freq_grid; ``bands=True`` selects the bands method of Section 3.1
-    (N_b = n_bands, N_t = trials_per_band) over the uniform grid."""
+    (N_b = n_bands, N_t = trials_per_band) over the uniform grid; ``exclude``
+    holds the spurious-period windows of Section 6.1 as (f_lo, f_hi) pairs."""
     mode = CP_SEARCH_BANDS if bands else (CP_SEARCH_COARSE_FINE if hierarchical else CP_SEARCH_FULL)
-    return cp_freq_grid(float(f_min), float(df), int(n_freq), mode, int(top_k),
-                        float(coarse_df), float(fine_df), float(fine_halfwidth), int(n_bands), int(trials_per_band))
+    ex = np.ascontiguousarray(np.asarray(exclude if exclude is not None else (), np.float64).reshape(-1))
+    if ex.size % 2:
+        raise ValueError("exclude holds (f_lo, f_hi) pairs")
+    g = cp_freq_grid(float(f_min), float(df), int(n_freq), mode, int(top_k),
+                     float(coarse_df), float(fine_df), float(fine_halfwidth), int(n_bands), int(trials_per_band),
+                     int(ex.size // 2), 0, ex.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if ex.size else None)
+    g._exclude_keep = ex          # the pointer above refers to this array
+    return g
 
 
 class Plan:
@@ -445,4 +456,5 @@ def cp_whiten(times, mags, offsets, p0, window=30, out=None, stream=None):
 def grid_from(g) -> cp_freq_grid:
     """cp_freq_grid from any object with the synthetic-grid attribute names."""
     return make_grid(g.f_min, g.df, g.n_freq, g.hierarchical, g.coarse_df, g.top_k, g.fine_df, g.fine_halfwidth,
-                     getattr(g, "bands", False), getattr(g, "n_bands", 0), getattr(g, "trials_per_band", 0))
+                     getattr(g, "bands", False), getattr(g, "n_bands", 0), getattr(g, "trials_per_band", 0),
+                     getattr(g, "exclude", ()))

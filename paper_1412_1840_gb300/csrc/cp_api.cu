@@ -100,6 +100,8 @@ struct cp_plan_s {
     bool bands = false;          // bands method (Section 3.1)
     int n_trials = 0;            // n_bands * trials_per_band
     int ex_lo = 1, ex_hi = 0;    // one-day grid indices (empty when ex_lo > ex_hi)
+    std::vector<double> excl_f;          // spurious-period windows [lo, hi] (Section 6.1)
+    std::vector<int32_t> excl_full, excl_coarse;   // their grid index ranges [k_lo, k_hi]
     int max_band_points = 0;
     double f_max = 0;
 
@@ -132,7 +134,10 @@ struct cp_plan_s {
     int8_t* d_band_of = nullptr;         // bands method
     int32_t* d_kept = nullptr;
     int32_t* d_trials = nullptr;
+    unsigned long long* d_wcand = nullptr;   // bands: FP32 window candidates per (curve, band)
     float* d_trial_stat = nullptr;
+    double* d_excl_f = nullptr;
+    int32_t *d_excl_full = nullptr, *d_excl_coarse = nullptr;
     float* d_W = nullptr;
     float* d_coarse = nullptr;
     int32_t *d_peaks = nullptr, *d_npeaks = nullptr;
@@ -171,6 +176,10 @@ struct cp_plan_s {
     bool ran = false;
     bool searched = false;    // a best-period search completed (trial list valid)
     bool capturing = false;   // inside build_graph's stream capture
+    cp_tuning tune{};         // copy of the caller's tuning table (has_tune)
+    bool has_tune = false;
+    int64_t replans = 0;      // plans rebuilt because a curve's sigma_t left its class
+    float* last_out = nullptr;   // output of the last cp_periodogram (re-run after a re-plan)
 };
 
 namespace {
@@ -209,7 +218,7 @@ double harmonic_tail(double sigma_t, int n)
 // tail stays below 1e-4 of the kernel peak; 0 (direct form) when even 32 harmonics do
 // not reach it (sigma_t below about 0.13).  The tail falls as sigma_t grows,
 // so each class is a threshold on sigma_t, found once by bisection.
-int harmonics_for(float sigma_t)
+const std::vector<double>& harmonic_thresholds()
 {
     static const std::vector<double> thr = [] {
         std::vector<double> t;
@@ -223,20 +232,34 @@ int harmonics_for(float sigma_t)
         }
         return t;
     }();
+    return thr;
+}
+
+int harmonics_for(float sigma_t)
+{
+    const std::vector<double>& thr = harmonic_thresholds();
     const int cls[4] = {8, 12, 16, 32};
     for (int k = 0; k < 4; k++)
         if ((double)sigma_t >= thr[k]) return cls[k];
     return 0;
 }
 
-double median_of_sorted(const float* v, int n)
+// Smallest sigma_t (as the FP32 value the kernels use) that harmonic class cls
+// covers; 0 for the direct form.
+float sigma_t_floor(int cls)
 {
-    return (n & 1) ? (double)v[n / 2] : 0.5 * ((double)v[n / 2 - 1] + (double)v[n / 2]);
+    const std::vector<double>& thr = harmonic_thresholds();
+    const int k = cls == 8 ? 0 : cls == 12 ? 1 : cls == 16 ? 2 : cls == 32 ? 3 : -1;
+    if (k < 0) return 0.f;
+    float f = (float)thr[k];
+    if ((double)f < thr[k]) f = std::nextafter(f, INFINITY);   // the first FP32 value harmonics_for accepts
+    return f;
 }
 
 // sigma_t of every curve as the plan sees it at creation time (to choose the
-// tensor form's harmonic count per curve).  The rule mode reads the current
-// magnitudes (copied from the device once when they live there).
+// tensor form's harmonic count per curve).  The rule mode evaluates the rule
+// on the device from the current magnitudes (one kernel; only the n_curves
+// results come back to the host).
 cp_status plan_sigma_t(cp_plan_t p, const cp_options& opt, std::vector<float>& st)
 {
     const int64_t nc = p->n_curves;
@@ -248,26 +271,60 @@ cp_status plan_sigma_t(cp_plan_t p, const cp_options& opt, std::vector<float>& s
         for (int64_t c = 0; c < nc; c++) st[c] = opt.sigma_t_per_curve[c];
         return CP_OK;
     }
-    std::vector<float> mags;
-    const float* m = p->mags;
-    if (!p->host_inputs) {
-        mags.resize((size_t)p->n_points);
-        CP_CUDA(cudaMemcpy(mags.data(), p->mags, (size_t)p->n_points * sizeof(float), cudaMemcpyDeviceToHost));
-        m = mags.data();
-    }
-    std::vector<float> y;
-    for (int64_t c = 0; c < nc; c++) {
-        const int64_t o = p->offsets[c];
-        const int n = (int)(p->offsets[c + 1] - o);
-        y.assign(m + o, m + o + n);
-        std::sort(y.begin(), y.end());
-        const int h = n / 2;
-        const double q2 = median_of_sorted(y.data(), n);
-        const double lq = median_of_sorted(y.data(), h), uq = median_of_sorted(y.data() + (n - h), h);
-        const double sk = (uq == lq) ? 0.0 : (uq + lq - 2.0 * q2) / (uq - lq);
-        st[c] = std::isfinite(sk) ? (float)(0.1 + 0.5 * std::exp(-12.0 * sk * sk)) : 0.1f;
+    const size_t npb = (size_t)p->n_points * sizeof(float);
+    const size_t ob = (size_t)(nc + 1) * sizeof(int64_t), sb = (size_t)nc * sizeof(float);
+    char* tmp = nullptr;
+    const size_t mb = p->host_inputs ? (npb + 255) / 256 * 256 : 0;
+    CP_CUDA(cudaMalloc(&tmp, mb + (ob + 255) / 256 * 256 + sb));
+    float* d_m = p->host_inputs ? reinterpret_cast<float*>(tmp) : const_cast<float*>(p->mags);
+    int64_t* d_off = reinterpret_cast<int64_t*>(tmp + mb);
+    float* d_st = reinterpret_cast<float*>(tmp + mb + (ob + 255) / 256 * 256);
+    cudaError_t e = cudaSuccess;
+    if (p->host_inputs) e = cudaMemcpyAsync(d_m, p->mags, npb, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, p->offsets.data(), ob, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = launch_sigma_t_rule(d_m, d_off, (int)nc, p->np2max, d_st, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st.data(), d_st, sb, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CP_ECUDA, std::string("cp_plan: sigma_t rule on the device: ") + cudaGetErrorString(e));
     }
     return CP_OK;
+}
+
+// Grid indices k in [0, n) with lo <= base + k * step <= hi, the frequency
+// evaluated in FP64 exactly as the search evaluates it (base + k*step, no
+// contraction); the frequency is non-decreasing in k, so the set is the range
+// [first, last] found by two bisections (empty when first > last).
+void grid_index_range(double base, double step, int64_t n, double lo, double hi, int32_t* out)
+{
+    auto f = [&](int64_t k) { return base + (double)k * step; };
+    int64_t a = 0, b = n;
+    while (a < b) {
+        const int64_t m = a + (b - a) / 2;
+        if (f(m) >= lo) b = m; else a = m + 1;
+    }
+    const int64_t first = a;
+    a = 0;
+    b = n;
+    while (a < b) {
+        const int64_t m = a + (b - a) / 2;
+        if (f(m) > hi) b = m; else a = m + 1;
+    }
+    const int64_t last = a - 1;
+    out[0] = (int32_t)std::min<int64_t>(first, INT32_MAX);
+    out[1] = (int32_t)std::max<int64_t>(last, -1);
+}
+
+Exclusion exclusion_of(cp_plan_t p)
+{
+    Exclusion e{};
+    e.n = (int32_t)(p->excl_f.size() / 2);
+    e.f = p->d_excl_f;
+    e.full_k = p->d_excl_full;
+    e.coarse_k = p->d_excl_coarse;
+    return e;
 }
 
 // Events recorded during capture must be external nodes to stay timeable;
@@ -394,6 +451,7 @@ PairArgs pair_args(cp_plan_t p, int stage, int w, float* out)
     a.coarse_out = p->d_coarse;
     a.best_key = best_keys(p);
     a.queue = queue_word(p, kQueuesPerWave * w + stage);
+    a.ex = exclusion_of(p);
     const std::vector<int64_t>* us;
     if (stage == kStageList) {
         a.unit_start = p->d_unit_list;
@@ -500,6 +558,7 @@ TensorArgs tensor_args(const PairArgs& d, cp_plan_t p)
     t.trials = d.trials;
     t.n_trials = d.n_trials;
     t.trial_stat = d.trial_stat;
+    t.ex = d.ex;
     return t;
 }
 
@@ -548,6 +607,8 @@ cp_status enqueue_search(cp_plan_t p, cudaStream_t s)
         wa.ph_base = p->d_ph_base;
         wa.ph_step = p->d_ph_full;
         wa.trials = p->d_trials;
+        wa.cand = p->d_wcand;
+        wa.exact_scans = reinterpret_cast<int*>(status_word(p)) + 1;   // high half of the status word
         wa.n_curves = (int)p->n_curves;
         wa.n_bands = p->grid.n_bands;
         wa.n_t = p->grid.trials_per_band;
@@ -576,6 +637,7 @@ cp_status enqueue_search(cp_plan_t p, cudaStream_t s)
             t.top_k = p->grid.top_k;
             t.peaks = p->d_peaks;
             t.n_peaks = p->d_npeaks;
+            t.ex = exclusion_of(p);
             CP_CUDA(launch_topk(t, s));
             if ((st = enqueue_pair(p, kStageFine, w, nullptr, s, &ev)) != CP_OK) return st;
         }
@@ -762,6 +824,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
                 return fail(CP_EINVAL, "cp_plan: tuning.tensor_classes must be a 4-bit mask");
         }
         opt.tuning = nullptr;   // copied; the caller's struct is not kept
+        p->tune = tune;
+        p->has_tune = true;
     }
     const cp_freq_grid g = *grid;
     if (!(std::isfinite(g.f_min) && g.f_min >= 0.0 && std::isfinite(g.df) && g.df > 0.0))
@@ -776,6 +840,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             return fail(CP_EINVAL, "cp_plan: n_bands must be in [1, 10]");
         if (g.trials_per_band < 1 || g.trials_per_band > kBandsMaxTrials)
             return fail(CP_EINVAL, "cp_plan: trials_per_band must be in [1, " + std::to_string(kBandsMaxTrials) + "]");
+        if (g.n_freq >= ((int64_t)1 << 29))
+            return fail(CP_EUNSUPPORTED, "cp_plan: the bands method supports grids of fewer than 2^29 points");
         p->bands = true;
         p->n_trials = g.n_bands * g.trials_per_band;
         // grid indices of the one-day frequencies |1/f - 1| < 1e-4 (a contiguous range; the
@@ -807,6 +873,24 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         p->J = (int)jd;
     }
 
+    // spurious-period exclusion windows (Section 6.1), copied; their index ranges on
+    // the uniform grid and (coarse-then-fine) on the coarse grid
+    if (g.n_exclude < 0 || g.n_exclude > CP_MAX_EXCLUDE)
+        return fail(CP_EINVAL, "cp_plan: n_exclude must be in [0, CP_MAX_EXCLUDE]");
+    if (g.n_exclude > 0 && !g.exclude) return fail(CP_EINVAL, "cp_plan: exclude is NULL");
+    for (int q = 0; q < g.n_exclude; q++) {
+        const double lo = g.exclude[2 * q], hi = g.exclude[2 * q + 1];
+        if (!(std::isfinite(lo) && std::isfinite(hi) && lo <= hi))
+            return fail(CP_EINVAL, "cp_plan: exclusion windows need finite lo <= hi");
+        p->excl_f.push_back(lo);
+        p->excl_f.push_back(hi);
+        int32_t r[2];
+        grid_index_range(g.f_min, g.df, g.n_freq, lo, hi, r);
+        p->excl_full.insert(p->excl_full.end(), r, r + 2);
+        grid_index_range(g.f_min, g.coarse_df, g.hierarchical == CP_SEARCH_COARSE_FINE ? p->kc : 0, lo, hi, r);
+        p->excl_coarse.insert(p->excl_coarse.end(), r, r + 2);
+    }
+
     // curve sizes
     if (offsets[0] != 0) return fail(CP_EINVAL, "cp_plan: offsets[0] must be 0");
     p->offsets.assign(offsets, offsets + n_curves + 1);
@@ -828,6 +912,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     p->max_n = max_n;
     while (p->np2max < max_n) p->np2max <<= 1;
     p->grid = g;
+    p->grid.exclude = nullptr;   // copied above; the caller's array is not kept
     p->opt = opt;
     p->times = times;
     p->mags = mags;
@@ -940,7 +1025,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     CP_CUDA(cudaMemGetInfo(&free_b, &total_b));
     size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 3);
     if (const char* env = std::getenv("CP_W_BUDGET_KB")) budget = (size_t)std::atoll(env) << 10;
-    const size_t tile16_bytes = (size_t)128 * 64 * 2, tile32_bytes = kTileFloats * sizeof(float);
+    const size_t tile16_bytes = tensor_tile_bytes(opt.dtype == CP_DTYPE_BF16), tile32_bytes = kTileFloats * sizeof(float);
     int64_t max_tiles32 = 0, max_tiles16 = 0;
     {
         auto close_wave = [&](int sb, int se) {
@@ -991,7 +1076,11 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         {(void**)&p->d_band_of, bnd ? (size_t)np : 0},
         {(void**)&p->d_kept, bnd ? (size_t)nc * g.n_bands * sizeof(int32_t) : 0},
         {(void**)&p->d_trials, bnd ? (size_t)nc * p->n_trials * sizeof(int32_t) : 0},
+        {(void**)&p->d_wcand, bnd ? (size_t)nc * 2 * p->n_trials * sizeof(unsigned long long) : 0},
         {(void**)&p->d_trial_stat, bnd ? (size_t)nc * p->n_trials * sizeof(float) : 0},
+        {(void**)&p->d_excl_f, p->excl_f.size() * sizeof(double)},
+        {(void**)&p->d_excl_full, p->excl_full.size() * sizeof(int32_t)},
+        {(void**)&p->d_excl_coarse, p->excl_coarse.size() * sizeof(int32_t)},
         {(void**)&p->d_W, (size_t)max_tiles32 * tile32_bytes},
         {(void**)&p->d_W16, (size_t)max_tiles16 * tile16_bytes},
         {(void**)&p->d_coef, p->tensor ? (size_t)nc * kCoefStride * sizeof(float) : 0},
@@ -1048,6 +1137,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         cps[c].off = offsets[c];
         cps[c].n = (int32_t)(offsets[c + 1] - offsets[c]);
         cps[c].fc = p->fc[c];
+        // per-curve classes follow sigma_t: a later sigma_t below the class's floor re-plans
+        cps[c].st_floor = (p->tensor && opt.n_max == 0) ? sigma_t_floor(p->cls[c]) : 0.f;
     }
     CP_CUDA(cudaMemcpy(p->d_cp, cps.data(), nc * sizeof(CurveParams), cudaMemcpyHostToDevice));
     CP_CUDA(cudaMemcpy(p->d_order, p->order.data(), nc * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -1057,6 +1148,13 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     CP_CUDA(cudaMemcpy(p->d_wtile, p->wtile.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
     if (bnd)
         CP_CUDA(cudaMemcpy(p->d_unit_list, p->unit_list.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (!p->excl_f.empty()) {
+        CP_CUDA(cudaMemcpy(p->d_excl_f, p->excl_f.data(), p->excl_f.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CP_CUDA(cudaMemcpy(p->d_excl_full, p->excl_full.data(), p->excl_full.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice));
+        CP_CUDA(cudaMemcpy(p->d_excl_coarse, p->excl_coarse.data(), p->excl_coarse.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice));
+    }
     if (opt.sigma_t_mode == CP_SIGMA_T_PER_CURVE) {
         for (int64_t c = 0; c < nc; c++)
             if (!(opt.sigma_t_per_curve[c] > 0.f && std::isfinite(opt.sigma_t_per_curve[c])))
@@ -1070,7 +1168,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     if (bnd) {
         int optin = 0;
         CP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-        if (window_smem_bytes(p->max_band_points, g.trials_per_band) + 4096 > (size_t)optin)
+        if (window_smem_bytes(p->max_band_points, g.trials_per_band) + 4096 > (size_t)optin ||
+            refine_smem_bytes(p->max_band_points, g.trials_per_band) > (size_t)optin)
             return fail(CP_EUNSUPPORTED, "cp_plan: spectral-window buffers do not fit in shared memory");
         CP_CUDA(prepare_bands_kernels(p->np2max, p->max_band_points, g.trials_per_band));
     }
@@ -1123,6 +1222,37 @@ cp_status cp_plan(const double* times, const float* mags, const float* errs, con
     return finish(CP_OK, "cp_plan");
 }
 
+// A call found a curve whose sigma_t (skewness rule on the current
+// magnitudes) lies below the floor of its planned harmonic class: the plan is
+// rebuilt on the device-computed sigma_t of the same inputs (schedule, buffers,
+// graph), and the caller repeats the call.
+static cp_status replan(cp_plan_t p)
+{
+    cp_plan_s* q = new (std::nothrow) cp_plan_s();
+    if (!q) return fail(CP_ENOMEM, "re-plan: host allocation failed");
+    cp_options o = p->opt;
+    o.tuning = p->has_tune ? &p->tune : nullptr;
+    cp_freq_grid g = p->grid;
+    g.exclude = p->excl_f.empty() ? nullptr : p->excl_f.data();
+    const std::vector<int64_t> off = p->offsets;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cp_status st = plan_impl(p->times, p->mags, p->errs, off.data(), p->n_curves, &g, &o, p->stream, q);
+    cudaSetDevice(prev);
+    if (st != CP_OK) {
+        char msg[512];
+        std::strncpy(msg, cpk::last_error_buffer(), sizeof(msg) - 1);
+        msg[sizeof(msg) - 1] = 0;
+        cp_destroy(q);
+        return cpk::set_error(st, msg);
+    }
+    q->replans = p->replans + 1;
+    q->last_out = p->last_out;
+    std::swap(*p, *q);
+    cp_destroy(q);   // the previous plan's resources
+    return CP_OK;
+}
+
 static cp_status periodogram_impl(cp_plan_t p, float* out)
 {
     if (!p) return fail(CP_EINVAL, "cp_periodogram: NULL plan");
@@ -1142,6 +1272,7 @@ static cp_status periodogram_impl(cp_plan_t p, float* out)
     if (st == CP_OK)
         CP_CUDA(cudaMemcpyAsync(p->h_status, p->d_u64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->stream));
     p->ran = true;
+    p->last_out = out;
     cudaSetDevice(prev);
     return st;
 }
@@ -1151,15 +1282,40 @@ static cp_status sync_impl(cp_plan_t p)
     if (!p) return fail(CP_EINVAL, "cp_sync: NULL plan");
     CP_CUDA(cudaSetDevice(p->device));
     CP_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->ran && (*p->h_status & 4) && !(*p->h_status & 3)) {
+        // the last periodogram used a harmonic count too small for a curve's new sigma_t
+        cp_status st = replan(p);
+        if (st == CP_OK) st = periodogram_impl(p, p->last_out);
+        if (st != CP_OK) return st;
+        CP_CUDA(cudaStreamSynchronize(p->stream));
+    }
     if (p->ran && (*p->h_status & 2))
         return fail(CP_ETIMEOUT, "a bounded device wait of the tensor-core kernel gave up");
-    if (p->ran && *p->h_status)
+    if (p->ran && (*p->h_status & 1))
         return fail(CP_EINVAL, "input contains a non-finite value, a zero median error bar or a bad sigma_t");
     return CP_OK;
 }
 
+static cp_status search_once(cp_plan_t p, int64_t* best_idx, double* best_freq, float* best_stat,
+                             uint8_t* is_periodic, float* psnr);
+
 static cp_status best_period_impl(cp_plan_t p, int64_t* best_idx, double* best_freq, float* best_stat,
                                   uint8_t* is_periodic, float* psnr)
+{
+    cp_status st = search_once(p, best_idx, best_freq, best_stat, is_periodic, psnr);
+    // a curve's sigma_t left the range its planned harmonic count covers: re-plan
+    // on the device-computed sigma_t and search again (the inputs are unchanged,
+    // so the new plan's classes cover every curve)
+    if (st == CP_OK && p && (*p->h_status & 4)) {
+        if ((st = replan(p)) == CP_OK) st = search_once(p, best_idx, best_freq, best_stat, is_periodic, psnr);
+        if (st == CP_OK && (*p->h_status & 4))
+            return fail(CP_ESTATE, "cp_best_period: the magnitudes changed during the call");
+    }
+    return st;
+}
+
+static cp_status search_once(cp_plan_t p, int64_t* best_idx, double* best_freq, float* best_stat,
+                             uint8_t* is_periodic, float* psnr)
 {
     if (!p) return fail(CP_EINVAL, "cp_best_period: NULL plan");
     int prev = 0;
@@ -1194,7 +1350,7 @@ static cp_status best_period_impl(cp_plan_t p, int64_t* best_idx, double* best_f
     if (psnr) std::memcpy(psnr, p->h_res_psnr, nc * sizeof(float));
     cudaSetDevice(prev);
     if (*p->h_status & 2) return fail(CP_ETIMEOUT, "a bounded device wait of the tensor-core kernel gave up");
-    if (*p->h_status)
+    if (*p->h_status & 1)
         return fail(CP_EINVAL, "input contains a non-finite value, a zero median error bar or a bad sigma_t");
     return CP_OK;
 }
@@ -1274,9 +1430,12 @@ cp_status cp_get_plan_info(cp_plan_t p, cp_plan_info* info)
     info->window_terms_search = p->window_terms;
     double wd = 0, wt = 0;
     for (const Wave& w : p->waves)
-        (w.cls ? wt : wd) += (double)(w.tile_end - w.tile_begin) * (w.cls ? 128.0 * 64 * 2 : (double)kTileFloats * 4);
+        (w.cls ? wt : wd) += (double)(w.tile_end - w.tile_begin) *
+                             (w.cls ? (double)tensor_tile_bytes(p->opt.dtype == CP_DTYPE_BF16) : (double)kTileFloats * 4);
     info->w_bytes_direct = wd;
     info->w_bytes_tensor = wt;
+    info->replans = p->replans;
+    info->bands_exact_scans = p->bands ? (int64_t)(*p->h_status >> 32) : 0;
     return CP_OK;
 }
 

@@ -7,10 +7,18 @@
 //             the bands in descending order of D (equal D: lower band first)
 //   k_window  one CTA per (curve, kept band): the spectral window of
 //             Eq. (bands), S(f_k) = |sum_{i in band} exp(i 2 pi f_k t_i)|^2,
-//             on the uniform grid f_k = f_min + k df, one segment of the grid
-//             at a time in shared memory; each segment's n_t highest local
-//             maxima (one-day frequencies left out) by a four-pass radix
-//             select on the value bits, merged into a running sorted list.
+//             on the uniform grid f_k = f_min + k df in FP32, one segment of
+//             the grid at a time in shared memory; the 2 n_t highest points
+//             that may be local maxima within the FP32 error bound (one-day
+//             frequencies left out) by a four-pass radix select on the value
+//             bits, merged into a running sorted candidate list, each
+//             candidate marked when its local-maximum test is certain.
+//   k_window_refine  one warp per (curve, kept band): the exact choice.  Every
+//             candidate whose local-maximum test, or whose order against a
+//             neighbour in the list, lies within the FP32 error bound gets
+//             its window value(s) again in FP64 from the exact phases; the
+//             n_t highest true local maxima (value descending, ties to the
+//             lower k) are the trials, identical to an FP64 evaluation.
 //
 // Phases: exp(i 2 pi f_k t_i) with t_i - t0 (the window is invariant to a
 // common time shift) from the exact 64-bit fixed-point phases
@@ -31,6 +39,12 @@ constexpr int kWinThreads = 256;
 constexpr int kWinRun = 16;                    // frequencies per thread per pass (stride kWinThreads)
 constexpr int kWinHalf = kWinRun / 2;          // q and q + kWinHalf share an f32x2 register
 constexpr int kWinSeg = 2 * kWinThreads * kWinRun - 2;   // grid points per segment (two passes with neighbours)
+// |S_fp32 - S_exact| <= kWinErr m^2 for a band of m > 1 samples: each term
+// exp(i x) carries the SFU sincos error (< 2^-20.5 absolute) plus at most 15
+// FP32 rotations (~2^-23 each), and |S| <= m^2; the bound leaves a margin of
+// about two.  Bands of one sample are exact (S = 1).
+constexpr float kWinErr = 2e-5f;
+__host__ __device__ constexpr int win_candidates(int n_t) { return 2 * n_t; }
 
 // ===========================================================================
 // k_bands
@@ -155,8 +169,19 @@ __host__ __device__ inline WinLayout win_layout(int max_band_points, int n_t)
     L.pts = (L.pts + 15) & ~(size_t)15;
     L.rot = L.pts + (size_t)max_band_points * sizeof(ulonglong2);
     L.lists = L.rot + (size_t)max_band_points * sizeof(float4);
-    L.total = L.lists + 3 * (size_t)pow2_at_least(n_t) * sizeof(unsigned long long);
+    L.total = L.lists + 3 * (size_t)pow2_at_least(win_candidates(n_t)) * sizeof(unsigned long long);
     return L;
+}
+
+// Candidate key: the FP32 window value, then bit 31 set when the point's
+// local-maximum test is certain (both comparisons decided by more than e2),
+// then the lower grid index k.
+__device__ __forceinline__ unsigned long long win_key(const float* S, int x, int k, int K, float e2)
+{
+    const float v = S[x];
+    const bool sure = (k == 0 || v > S[x - 1] + e2) && (k == K - 1 || v > S[x + 1] + e2);
+    return ((unsigned long long)orderable(v) << 32) | (sure ? 0x80000000ull : 0ull) |
+           (unsigned long long)(0x7fffffffu - (uint32_t)k);
 }
 
 __device__ __forceinline__ bool win_cand(const uint32_t* mask, int j)
@@ -202,7 +227,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
     uint32_t* mask = reinterpret_cast<uint32_t*>(smem + Lo.mask);
     ulonglong2* pts = reinterpret_cast<ulonglong2*>(smem + Lo.pts);
     float4* rot = reinterpret_cast<float4*>(smem + Lo.rot);
-    const int cap = pow2_at_least(a.n_t);
+    const int cap = pow2_at_least(win_candidates(a.n_t));
     unsigned long long* sel = reinterpret_cast<unsigned long long*>(smem + Lo.lists);
     unsigned long long* run0 = sel + cap;
     unsigned long long* run1 = run0 + cap;
@@ -215,7 +240,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kWinThreads / 32;
     const int c = blockIdx.x / a.n_bands, b = blockIdx.x - c * a.n_bands;
-    const int K = a.n_freq, n_t = a.n_t;
+    const int K = a.n_freq, n_t = win_candidates(a.n_t);   // candidates kept per band
     const int64_t off = a.cp[c].off;
     const int n = a.cp[c].n;
     const int band = a.kept[(int64_t)c * a.n_bands + b];
@@ -250,6 +275,8 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
         __syncthreads();
     }
     const int m = min(s_m, a.max_band_points);
+    // two error bounds apart: a comparison decided by more is the same in exact arithmetic
+    const float e2 = m <= 1 ? 0.f : 2.f * kWinErr * (float)m * (float)m;
 
     unsigned long long* run = run0;   // running list: the n_t highest so far, descending
     unsigned long long* nxt = run1;
@@ -306,9 +333,10 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
         if (tid == 0) { s_total = 0; s_nsel = 0; }
         __syncthreads();
 
-        // 3. admissible local maxima of the segment: S[k] > S[k-1], S[k] >= S[k+1]
-        //    (grid ends: one neighbour), one-day frequencies left out; once the running
-        //    list is full, only keys above its last entry can still enter it
+        // 3. candidates of the segment: points that can be local maxima S[k] > S[k-1],
+        //    S[k] >= S[k+1] (grid ends: one neighbour) within the error bound, one-day
+        //    frequencies left out; once the running list is full, only keys above its
+        //    last entry can still enter it
         const unsigned long long floor_key = rc == n_t ? run[n_t - 1] : 0ull;
         const int len = hi - lo;
         const int words = (len + 31) >> 5;
@@ -320,8 +348,9 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
             if (j < len) {
                 const int x = k - v0;
                 const float v = S[x];
-                ok = (k == 0 || v > S[x - 1]) && (k == K - 1 || v >= S[x + 1]) && !(k >= a.ex_lo && k <= a.ex_hi) &&
-                     (((unsigned long long)orderable(v) << 32) | (0xffffffffu - (uint32_t)k)) > floor_key;
+                const bool lok = k == 0 || (e2 > 0.f ? v >= S[x - 1] - e2 : v > S[x - 1]);
+                const bool rok = k == K - 1 || v >= S[x + 1] - e2;
+                ok = lok && rok && !(k >= a.ex_lo && k <= a.ex_hi) && win_key(S, x, k, K, e2) > floor_key;
             }
             const uint32_t bal = __ballot_sync(0xffffffffu, ok);
             if (lane == 0) {
@@ -403,7 +432,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
                 const uint32_t key = orderable(S[lo + j - v0]);
                 if (key > T || (key == T && take_all_eq && total > n_t)) {
                     const int pos = atomicAdd(&s_nsel, 1);
-                    if (pos < n_t) sel[pos] = ((unsigned long long)key << 32) | (0xffffffffu - (uint32_t)(lo + j));
+                    if (pos < n_t) sel[pos] = win_key(S, lo + j - v0, lo + j, K, e2);
                 }
             }
         }
@@ -426,7 +455,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
                     const int r = before + __popc(bal & ((1u << lane) - 1u));
                     if (r < need) {
                         const int pos = atomicAdd(&s_nsel, 1);
-                        if (pos < n_t) sel[pos] = ((unsigned long long)T << 32) | (0xffffffffu - (uint32_t)(lo + j));
+                        if (pos < n_t) sel[pos] = win_key(S, lo + j - v0, lo + j, K, e2);
                     }
                 }
                 taken += chunk;
@@ -455,9 +484,192 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
         __syncthreads();
     }
 
-    int32_t* out = a.trials + ((int64_t)c * a.n_bands + b) * n_t;
-    for (int r = tid; r < n_t; r += kWinThreads)
-        out[r] = r < rc ? (int32_t)(0xffffffffu - (uint32_t)(run[r] & 0xffffffffu)) : -1;
+    unsigned long long* out = a.cand + ((int64_t)c * a.n_bands + b) * n_t;
+    for (int r = tid; r < n_t; r += kWinThreads) out[r] = r < rc ? run[r] : 0ull;
+}
+
+// ===========================================================================
+// k_window_refine: one warp per (curve, kept band), see the file header.
+// ===========================================================================
+constexpr int kRefineWarps = 8;
+
+// Exact window value at grid index k from the band's 64-bit fixed-point phases
+// (lanes split the points; FP64 sincospi of the exactly reduced angle).
+__device__ double window_fp64(const ulonglong2* pts, int m, uint64_t k, int lane)
+{
+    if (m <= 1) return (double)m;
+    double re = 0.0, im = 0.0;
+    for (int p = lane; p < m; p += 32) {
+        const uint64_t U = pts[p].x + k * pts[p].y;              // frac(f_k (t - t0)) in 2^-64 turns
+        double sv, cv;
+        sincospi((double)(int64_t)U * 0x1p-63, &sv, &cv);        // angle 2 pi U / 2^64 in (-pi, pi]
+        re += cv;
+        im += sv;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    return re * re + im * im;
+}
+
+// The same value computed by one lane alone (points in sample order).
+__device__ double window_fp64_lane(const ulonglong2* pts, int m, uint64_t k)
+{
+    if (m <= 1) return (double)m;
+    double re = 0.0, im = 0.0;
+    for (int p = 0; p < m; p++) {
+        const uint64_t U = pts[p].x + k * pts[p].y;
+        double sv, cv;
+        sincospi((double)(int64_t)U * 0x1p-63, &sv, &cv);
+        re += cv;
+        im += sv;
+    }
+    return re * re + im * im;
+}
+
+// Lane 0 keeps the n_t best (value descending, ties to the lower k) in val/kk;
+// candidates arrive in ascending k, so an equal value goes after the others.
+__device__ __forceinline__ void list_insert(double* val, int32_t* kk, int& cnt, int n_t, double v, int k)
+{
+    if (cnt == n_t && !(v > val[n_t - 1])) return;
+    int q = cnt < n_t ? cnt : n_t - 1;
+    while (q > 0 && val[q - 1] < v) {
+        val[q] = val[q - 1];
+        kk[q] = kk[q - 1];
+        q--;
+    }
+    val[q] = v;
+    kk[q] = k;
+    if (cnt < n_t) cnt++;
+}
+
+__global__ void __launch_bounds__(32 * kRefineWarps) k_window_refine(const WindowArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int job = blockIdx.x * kRefineWarps + warp;       // (curve, kept band)
+    if (job >= a.n_curves * a.n_bands) return;
+    const int c = job / a.n_bands, b = job - c * a.n_bands;
+    const int K = a.n_freq, n_t = a.n_t, nc = win_candidates(n_t);
+    ulonglong2* pts = reinterpret_cast<ulonglong2*>(smem) + (size_t)warp * a.max_band_points;
+    // per candidate: value (FP32 from the window, or FP64 where recomputed) and the grid
+    // index with flags (bit 30: local-maximum test uncertain, bit 29: recompute)
+    unsigned char* vbase = smem + (size_t)kRefineWarps * a.max_band_points * sizeof(ulonglong2);
+    double* val = reinterpret_cast<double*>(vbase) + (size_t)warp * nc;
+    int32_t* kk = reinterpret_cast<int32_t*>(vbase + (size_t)kRefineWarps * nc * sizeof(double)) + (size_t)warp * nc;
+    const int64_t off = a.cp[c].off;
+    const int n = a.cp[c].n;
+    const int band = a.kept[(int64_t)c * a.n_bands + b];
+
+    // the band's exact phases, in sample order
+    int m = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const bool in = i < n && a.band_of[off + i] == band;
+        const uint32_t bal = __ballot_sync(0xffffffffu, in);
+        const int pos = m + __popc(bal & ((1u << lane) - 1u));
+        if (in && pos < a.max_band_points) pts[pos] = make_ulonglong2(a.ph_base[off + i], a.ph_step[off + i]);
+        m += __popc(bal);
+    }
+    m = min(m, a.max_band_points);
+    __syncwarp();
+    const float dl = m <= 1 ? 0.f : kWinErr * (float)m * (float)m;   // |S_fp32 - S| bound
+
+    // candidates (descending FP32 value, then sure-first, then lower k)
+    const unsigned long long* cand = a.cand + (int64_t)job * nc;
+    int cnt = 0;
+    for (int r0 = 0; r0 < nc; r0 += 32) {          // every lane takes every trip (the ballot needs all 32)
+        const int r = r0 + lane;
+        const unsigned long long key = r < nc ? cand[r] : 0ull;
+        if (key) {
+            val[r] = (double)from_orderable((uint32_t)(key >> 32));
+            kk[r] = (int32_t)(0x7fffffffu - (uint32_t)(key & 0x7fffffffu)) | (int32_t)((key & 0x80000000ull) ? 0 : 0x40000000);
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, key != 0ull);
+        cnt += __popc(bal);
+    }
+    __syncwarp();
+    const float last32 = cnt > 0 ? (float)val[cnt - 1] : 0.f;
+    const bool full = cnt == nc;
+
+    // which candidates need the exact value: an uncertain local-maximum test, or a
+    // neighbour in the list closer than two error bounds (order undecided)
+    for (int r = lane; r < cnt; r += 32) {
+        const bool unsure = (kk[r] & 0x40000000) != 0;
+        const double v = val[r];
+        const bool close = (r > 0 && val[r - 1] - v <= 2.0 * dl) || (r + 1 < cnt && v - val[r + 1] <= 2.0 * dl);
+        if (unsure || close) kk[r] |= 0x20000000;
+    }
+    __syncwarp();
+    for (int r = 0; r < cnt; r++) {
+        const int tag = kk[r];
+        if (!(tag & 0x20000000)) continue;
+        const int k = tag & 0x1fffffff;
+        const double sk = window_fp64(pts, m, (uint64_t)k, lane);
+        bool keep = true;
+        if (tag & 0x40000000) {     // the local-maximum test in exact values
+            if (k > 0) keep = sk > window_fp64(pts, m, (uint64_t)(k - 1), lane);
+            if (keep && k < K - 1) keep = sk >= window_fp64(pts, m, (uint64_t)(k + 1), lane);
+        }
+        if (lane == 0) {
+            val[r] = sk;
+            if (!keep) kk[r] = -1;
+        }
+        __syncwarp();
+    }
+
+    // the true maxima by value descending, ties to the lower k (insertion sort: only
+    // the recomputed entries can be out of place), the first n_t are the trials
+    int32_t* out = a.trials + (int64_t)job * n_t;
+    int scan = 0;
+    if (lane == 0) {
+        int kept = 0;
+        for (int r = 0; r < cnt; r++) {
+            if (kk[r] < 0) continue;
+            const double v = val[r];
+            const int k = kk[r] & 0x1fffffff;
+            int q = kept;
+            while (q > 0 && (val[q - 1] < v || (val[q - 1] == v && (kk[q - 1] & 0x1fffffff) > k))) {
+                val[q] = val[q - 1];
+                kk[q] = kk[q - 1];
+                q--;
+            }
+            val[q] = v;
+            kk[q] = k;
+            kept++;
+        }
+        for (int r = 0; r < n_t; r++) out[r] = r < kept ? (kk[r] & 0x1fffffff) : -1;
+        // a full candidate list leaves out points whose FP32 value is below its last
+        // entry: they cannot reach the trials when the n_t-th trial lies above it by
+        // more than two error bounds; otherwise (peaks of nearly equal height, such
+        // as the maxima 4 of a two-sample band) the band is scanned exactly
+        scan = full && (kept < n_t || val[n_t - 1] - (double)dl <= (double)last32 + (double)dl);
+    }
+    scan = __shfl_sync(0xffffffffu, scan, 0);
+    if (!scan) return;
+    if (lane == 0) atomicAdd(a.exact_scans, 1);
+
+    // exact scan of the whole grid: lanes take k = k0 + lane, k0 advancing by 30 so that
+    // lanes 1..30 have both neighbours; S(-1) = S(K) = -inf reproduce the end rules
+    int cntl = 0;
+    for (int k0 = -1; k0 + 1 < K; k0 += 30) {
+        const int k = k0 + lane;
+        const double v = (k >= 0 && k < K) ? window_fp64_lane(pts, m, (uint64_t)k) : -INFINITY;
+        const double left = __shfl_up_sync(0xffffffffu, v, 1), right = __shfl_down_sync(0xffffffffu, v, 1);
+        const bool ismax = lane >= 1 && lane <= 30 && k < K && v > left && v >= right && !(k >= a.ex_lo && k <= a.ex_hi);
+        uint32_t bal = __ballot_sync(0xffffffffu, ismax);
+        while (bal) {
+            const int l = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const double vv = __shfl_sync(0xffffffffu, v, l);
+            if (lane == 0) list_insert(val, kk, cntl, n_t, vv, k0 + l);
+        }
+    }
+    __syncwarp();
+    if (lane == 0)
+        for (int r = 0; r < n_t; r++) out[r] = r < cntl ? kk[r] : -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -465,9 +677,17 @@ size_t bands_smem_bytes(int np2max) { return (size_t)np2max * (sizeof(unsigned l
 
 size_t window_smem_bytes(int max_band_points, int n_t) { return win_layout(max_band_points, n_t).total; }
 
+size_t refine_smem_bytes(int max_band_points, int n_t)
+{
+    return (size_t)kRefineWarps * ((size_t)max_band_points * sizeof(ulonglong2) +
+                                   (size_t)win_candidates(n_t) * (sizeof(double) + sizeof(int32_t)));
+}
+
 cudaError_t prepare_bands_kernels(int np2max, int max_band_points, int n_t)
 {
     cudaError_t e = raise_dyn_smem((const void*)k_bands, bands_smem_bytes(np2max));
+    if (e != cudaSuccess) return e;
+    e = raise_dyn_smem((const void*)k_window_refine, refine_smem_bytes(max_band_points, n_t));
     if (e != cudaSuccess) return e;
     return raise_dyn_smem((const void*)k_window, window_smem_bytes(max_band_points, n_t));
 }
@@ -483,6 +703,10 @@ cudaError_t launch_window(const WindowArgs& a, cudaStream_t s)
     const int64_t ctas = (int64_t)a.n_curves * a.n_bands;
     if (ctas <= 0) return cudaSuccess;
     k_window<<<(unsigned)ctas, kWinThreads, window_smem_bytes(a.max_band_points, a.n_t), s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_window_refine<<<(unsigned)((ctas + kRefineWarps - 1) / kRefineWarps), 32 * kRefineWarps,
+                      refine_smem_bytes(a.max_band_points, a.n_t), s>>>(a);
     return cudaGetLastError();
 }
 

@@ -44,7 +44,27 @@ struct CurveParams {
     float gamma;      // magnitude scale
     double ip;        // FP64 ip
     double t0;        // min t of the curve
+    float st_floor;   // smallest sigma_t the curve's planned evaluation class covers
+                      // (tensor form: its harmonic count's truncation target; else 0)
 };
+
+// sigma_t = 0.1 + 0.5 exp(-12 S^2), S the Bowley skewness of the magnitudes
+// with quartiles = medians of the lower and upper halves of the sorted values
+// (the middle value excluded for odd N), S = 0 when Q3 = Q1: the rule that
+// Section 3 keeps in the paper's source as commented-out text.  `ys` holds
+// the curve's n magnitudes in ascending order.
+__device__ __forceinline__ double median_of_sorted(const float* s, int n)
+{
+    return (n & 1) ? (double)s[n >> 1] : 0.5 * ((double)s[(n >> 1) - 1] + (double)s[n >> 1]);
+}
+__device__ __forceinline__ double sigma_t_rule(const float* ys, int n)
+{
+    const int h = n >> 1;
+    const double q2 = median_of_sorted(ys, n);
+    const double lq = median_of_sorted(ys, h), uq = median_of_sorted(ys + (n - h), h);
+    const double sk = (uq == lq) ? 0.0 : (uq + lq - 2.0 * q2) / (uq - lq);
+    return 0.1 + 0.5 * exp(-12.0 * sk * sk);
+}
 
 // Search stages.
 // kStageList evaluates an explicit per-curve list of grid indices (the trial
@@ -63,6 +83,38 @@ __host__ __device__ inline int tiles_of(int n)
 {
     const int nb = (n + kTile - 1) / kTile;
     return nb * (nb + 1) / 2;
+}
+
+// Spurious-period exclusion windows (Section 6.1): closed frequency intervals,
+// as FP64 bounds (checked against a computed frequency) and as the index
+// ranges [k_lo, k_hi] they cover on the uniform grid (full_k) and on the
+// coarse grid (coarse_k).  n = 0: no windows.
+struct Exclusion {
+    int32_t n;
+    const double* f;          // [2n] lo, hi
+    const int32_t* full_k;    // [2n]
+    const int32_t* coarse_k;  // [2n]
+};
+
+__device__ __forceinline__ bool excluded_k(const int32_t* r, int n, int64_t k)
+{
+    for (int q = 0; q < n; q++)
+        if (k >= r[2 * q] && k <= r[2 * q + 1]) return true;
+    return false;
+}
+
+__device__ __forceinline__ bool excluded_f(const Exclusion& e, double f)
+{
+    for (int q = 0; q < e.n; q++)
+        if (f >= e.f[2 * q] && f <= e.f[2 * q + 1]) return true;
+    return false;
+}
+
+// base + k * step in FP64 without contraction: the expression the search and
+// its frequency outputs use everywhere.
+__device__ __forceinline__ double grid_freq(double base, double k, double step)
+{
+    return __dadd_rn(base, __dmul_rn(k, step));
 }
 
 struct PairArgs {
@@ -93,6 +145,7 @@ struct PairArgs {
     const int32_t* trials;       // list stage: [n_curves * n_trials] grid indices, -1 = none
     int32_t n_trials;
     float* trial_stat;           // list stage: nCKP per trial (may be null)
+    Exclusion ex;                // spurious-period windows (Section 6.1)
 };
 
 struct StatsArgs {
@@ -133,6 +186,7 @@ struct TopkArgs {
     int top_k;
     int32_t* peaks;
     int32_t* n_peaks;
+    Exclusion ex;                 // excluded coarse points are not peak candidates
 };
 
 struct FinalArgs {
@@ -198,6 +252,7 @@ struct TensorArgs {
     const int32_t* trials;        // list stage (as in PairArgs)
     int32_t n_trials;
     float* trial_stat;
+    Exclusion ex;
 };
 
 // Bands method, Section 3.1 (cp_bands.cu).
@@ -220,6 +275,8 @@ struct WindowArgs {
     const uint64_t* ph_base;      // frac(f_min (t - t0)) in 2^-64 turns
     const uint64_t* ph_step;      // frac(df (t - t0))
     int32_t* trials;              // [n_curves * n_bands * n_t]
+    unsigned long long* cand;     // [n_curves * n_bands * 2 n_t] FP32 candidates (window -> refine)
+    int* exact_scans;             // lists chosen by a whole-grid FP64 scan (completeness unproven)
     int n_curves, n_bands, n_t;
     int n_freq;
     int ex_lo, ex_hi;             // one-day grid indices [ex_lo, ex_hi] (ex_lo > ex_hi: none)
@@ -228,11 +285,13 @@ struct WindowArgs {
 
 size_t bands_smem_bytes(int np2max);
 size_t window_smem_bytes(int max_band_points, int n_t);
+size_t refine_smem_bytes(int max_band_points, int n_t);
 cudaError_t prepare_bands_kernels(int np2max, int max_band_points, int n_t);
 cudaError_t launch_bands(const BandsArgs& a, int n_curves, cudaStream_t s);
 cudaError_t launch_window(const WindowArgs& a, cudaStream_t s);
 
-size_t tensor_smem_bytes();
+size_t tensor_smem_bytes(bool bf16);
+size_t tensor_tile_bytes(bool bf16);   // bytes of one stored W' tile (BF16: hi and lo parts)
 int tensor_tiles_of(int n);
 cudaError_t prepare_tensor_kernel(int n_max);
 cudaError_t launch_build_w16(const BuildW16Args& a, cudaStream_t s);
@@ -250,6 +309,11 @@ int pair_direct_threads();
 cudaError_t pair_direct_occupancy(int* blocks_per_sm, size_t smem);
 size_t stats_smem_bytes(int np2max);
 cudaError_t prepare_kernels(int np2max, size_t pair_smem);
+// sigma_t of the skewness rule for every curve (one CTA per curve), from
+// device magnitudes and device CSR offsets: the plan uses it to choose the
+// tensor form's harmonic count per curve.
+cudaError_t launch_sigma_t_rule(const float* mags, const int64_t* offsets, int n_curves, int np2max, float* out,
+                                cudaStream_t s);
 
 // Raises a kernel's dynamic shared-memory limit on the current device to at
 // least `bytes`; never lowers it.  The limit is process-wide per device, so

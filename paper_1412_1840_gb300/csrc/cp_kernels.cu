@@ -30,10 +30,7 @@ __constant__ float c_th[8] = {0.4584f, 0.4565f, 0.4537f, 0.4581f, 0.5875f, 1.115
 
 constexpr int kStatsThreads = 256;
 
-__device__ __forceinline__ double median_sorted(const float* s, int n)
-{
-    return (n & 1) ? (double)s[n >> 1] : 0.5 * ((double)s[(n >> 1) - 1] + (double)s[n >> 1]);
-}
+__device__ __forceinline__ double median_sorted(const float* s, int n) { return median_of_sorted(s, n); }
 
 // Quantile by linear interpolation between order statistics at q*(n-1).
 __device__ __forceinline__ double quantile_sorted(const float* s, int n, double q)
@@ -130,16 +127,14 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsArgs a)
         if (a.sigma_t_mode == 1) {
             st = (double)a.sigma_t_per_curve[c];
         } else if (a.sigma_t_mode == 2) {
-            // Bowley skewness, quartiles = medians of the lower / upper halves
-            const int h = n >> 1;
-            const double lq = median_sorted(ys, h), uq = median_sorted(ys + (n - h), h);
-            const double sk = (uq == lq) ? 0.0 : (uq + lq - 2.0 * yref) / (uq - lq);
-            st = 0.1 + 0.5 * exp(-12.0 * sk * sk);
+            st = sigma_t_rule(ys, n);
         } else {
             st = (double)a.sigma_t;
         }
         if (!(sy > 0.0) || !isfinite(sy) || !(st > 0.0) || !isfinite(st)) s_bad = 1;
         const float stf = (float)st;
+        // the planned harmonic count no longer covers this sigma_t: the host re-plans
+        if (stf < P->st_floor) atomicOr(a.status, 4);
         P->sigma_y = (float)sy;
         P->sigma_t = stf;
         P->psnr = (float)psnr;
@@ -209,6 +204,38 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsArgs a)
             a.ph_fine[off + i] = fixfrac(a.fine_df, tp);
         }
     }
+}
+
+// ===========================================================================
+// k_sigma_t_rule: sigma_t of the skewness rule per curve (one CTA per curve),
+// the same sort and the same FP64 arithmetic as k_stats.
+// ===========================================================================
+__global__ void __launch_bounds__(kStatsThreads) k_sigma_t_rule(const float* mags, const int64_t* offsets,
+                                                               int np2max, float* out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* ys = reinterpret_cast<float*>(smem);
+    const int c = blockIdx.x, tid = threadIdx.x;
+    const int64_t off = offsets[c];
+    const int n = (int)(offsets[c + 1] - off);
+    int np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (int i = tid; i < np2; i += kStatsThreads) ys[i] = i < n ? mags[off + i] : INFINITY;
+    for (int k = 2; k <= np2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            __syncthreads();
+            for (int i = tid; i < np2; i += kStatsThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const float u = ys[i], v = ys[ixj];
+                    if ((u > v) == up) { ys[i] = v; ys[ixj] = u; }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) out[c] = (float)sigma_t_rule(ys, n);
 }
 
 // ===========================================================================
@@ -629,6 +656,16 @@ cudaError_t launch_stats(const StatsArgs& a, int n_curves, cudaStream_t s)
 {
     const size_t smem = stats_smem_bytes(a.np2max);
     k_stats<<<n_curves, kStatsThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_t_rule(const float* mags, const int64_t* offsets, int n_curves, int np2max, float* out,
+                                cudaStream_t s)
+{
+    const size_t smem = (size_t)np2max * sizeof(float);
+    cudaError_t e = raise_dyn_smem((const void*)k_sigma_t_rule, smem);
+    if (e != cudaSuccess) return e;
+    k_sigma_t_rule<<<n_curves, kStatsThreads, smem, s>>>(mags, offsets, np2max, out);
     return cudaGetLastError();
 }
 

@@ -113,6 +113,8 @@ extern "C" cp_status cp_best_period_noalloc(const double* times, const float* ma
     int J = 0;
     if (g.hierarchical == CP_SEARCH_BANDS)
         return nfail(CP_EUNSUPPORTED, "cp_best_period_noalloc: the bands method needs a plan (cp_plan)");
+    if (g.n_exclude != 0)
+        return nfail(CP_EUNSUPPORTED, "cp_best_period_noalloc: exclusion windows need a plan (cp_plan)");
     if (g.hierarchical != CP_SEARCH_FULL && g.hierarchical != CP_SEARCH_COARSE_FINE)
         return nfail(CP_EINVAL, "cp_best_period_noalloc: bad search mode");
     if (g.hierarchical) {

@@ -38,10 +38,18 @@ namespace cpk {
 
 using namespace tc;
 
-constexpr int kTcStages = 3;
 constexpr int kTcA = 16384;            // 128 x 64 x 2 B
 constexpr int kTcB = 32768;            // 256 x 64 x 2 B
-constexpr int kTcStageBytes = 2 * kTcA + kTcB;   // W' tiles of two M-tiles + one Z tile
+// BF16 carries 8 significand bits, and the rounding of W' alone would exceed
+// the tolerance of 1e-3 (Z's rounding stays below it).  With BF16 operands W'
+// is therefore stored as two BF16 tiles, hi = bf16(w) and lo = bf16(w - hi),
+// and every K slice issues two MMAs into the same accumulator: W' carries ~16
+// significand bits, Z stays single.  FP16 (11 bits) needs no split.
+__host__ __device__ constexpr int tc_wparts(bool bf) { return bf ? 2 : 1; }
+// Stages of the operand ring: W' tiles (all parts) of two M-tiles + one Z tile.
+__host__ __device__ constexpr int tc_stages(bool bf) { return bf ? 2 : 3; }
+__host__ __device__ constexpr int tc_stage_bytes(bool bf) { return 2 * tc_wparts(bf) * kTcA + kTcB; }
+constexpr int kTcMaxStages = 3;
 constexpr int kTcCols = 256;           // columns per unit
 // Epilogue warps: 8 for up to 16 harmonics (two warps per TMEM lane group,
 // each taking half of the unit's frequencies), else 4; the drain of an
@@ -126,10 +134,12 @@ __global__ void __launch_bounds__(256) k_build_w16(const BuildW16Args a)
     const int kb = (threadIdx.x & 1) * 32;          // first of 32 columns
     const int i = I * 128 + r;
     const float ypi = i < n ? a.yp[P.off + i] : 0.f;
-    unsigned char* dst = reinterpret_cast<unsigned char*>(a.W16) + (T - a.tile_begin) * (int64_t)kTcA;
+    const bool bf = a.bf16 != 0;
+    // tile T: its tc_wparts(bf) parts (hi, then lo for BF16) of kTcA bytes each
+    unsigned char* dst = reinterpret_cast<unsigned char*>(a.W16) + (T - a.tile_begin) * (int64_t)(tc_wparts(bf) * kTcA);
 #pragma unroll
     for (int ch = 0; ch < 4; ch++) {
-        uint32_t packed[4];
+        uint32_t packed[4], packed_lo[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
             float v2[2];
@@ -141,9 +151,19 @@ __global__ void __launch_bounds__(256) k_build_w16(const BuildW16Args a)
                 if (i < n && j < n) w = ((gauss_g(ypi, a.yp[P.off + j]) - P.ip_hi) - P.ip_lo) * scale;
                 v2[h] = w;
             }
-            packed[e >> 1] = (uint32_t)to16(v2[0], a.bf16) | ((uint32_t)to16(v2[1], a.bf16) << 16);
+            const uint16_t h0 = to16(v2[0], bf), h1 = to16(v2[1], bf);
+            packed[e >> 1] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            if (bf) {
+                // the remainder w - hi is exact in FP32; its BF16 rounding is the lo part
+                const float l0 = v2[0] - __bfloat162float(__ushort_as_bfloat16(h0));
+                const float l1 = v2[1] - __bfloat162float(__ushort_as_bfloat16(h1));
+                packed_lo[e >> 1] = (uint32_t)to16(l0, true) | ((uint32_t)to16(l1, true) << 16);
+            }
         }
-        *reinterpret_cast<uint4*>(dst + sw128_offset(r, kb + ch * 8)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        const uint32_t o = sw128_offset(r, kb + ch * 8);
+        *reinterpret_cast<uint4*>(dst + o) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        if (bf)
+            *reinterpret_cast<uint4*>(dst + kTcA + o) = make_uint4(packed_lo[0], packed_lo[1], packed_lo[2], packed_lo[3]);
     }
 }
 
@@ -304,9 +324,13 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int STG = tc_stages(BF);                // operand ring stages
+    constexpr int SB = tc_stage_bytes(BF);            // bytes per stage
+    constexpr int WP = tc_wparts(BF);                 // W' parts (BF16: hi and lo)
+    constexpr int AB = WP * kTcA;                     // W' bytes of one M-tile in a stage
     // producers' phase table of the current unit: (phase at the unit's first frequency, step)
-    ulonglong2* sPh = reinterpret_cast<ulonglong2*>(smem + kTcStages * kTcStageBytes);
-    __shared__ uint64_t bar_afull[kTcStages], bar_bfull[kTcStages], bar_empty[kTcStages];
+    ulonglong2* sPh = reinterpret_cast<ulonglong2*>(smem + STG * SB);
+    __shared__ uint64_t bar_afull[kTcMaxStages], bar_bfull[kTcMaxStages], bar_empty[kTcMaxStages];
     __shared__ uint64_t bar_tfull, bar_tempty[2], bar_drain;
     __shared__ uint32_t s_taddr;
     __shared__ int s_abort;
@@ -336,11 +360,11 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     static_assert(!FOLD || NH % 2 == 0, "the producers take the step's sign from the parity of nn");
     // Stages produced concurrently.  A group owns every use of its stages, so
     // it never waits more than one barrier phase ahead; hence groups <= stages.
-    constexpr int groups = PROD / GS < kTcStages ? PROD / GS : kTcStages;
+    constexpr int groups = PROD / GS < STG ? PROD / GS : STG;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; s++) {
+        for (int s = 0; s < STG; s++) {
             mbar_init(&bar_afull[s], 1);
             mbar_init(&bar_bfull[s], items);
             mbar_init(&bar_empty[s], 1);
@@ -374,23 +398,23 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                     const int I0 = 2 * P, I1 = 2 * P + 1;
                     for (int J = 2 * I0; J < U.nkc; J++, q++) {
                         const bool use1 = I1 < U.nmt && J >= 2 * I1;
-                        const int s = q % kTcStages;
-                        if (!mbar_wait(&bar_empty[s], ((q / kTcStages) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
-                        unsigned char* st = smem + s * kTcStageBytes;
+                        const int s = q % STG;
+                        if (!mbar_wait(&bar_empty[s], ((q / STG) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
+                        unsigned char* st = smem + s * SB;
                         const unsigned char* w16 = reinterpret_cast<const unsigned char*>(a.W16);
-                        mbar_arrive_expect_tx(&bar_afull[s], use1 ? 2 * kTcA : kTcA);
-                        bulk_g2s(st, w16 + (U.wbase + tc_tile_index(I0, J, U.nkc)) * (int64_t)kTcA, kTcA, &bar_afull[s]);
+                        mbar_arrive_expect_tx(&bar_afull[s], use1 ? 2 * AB : AB);
+                        bulk_g2s(st, w16 + (U.wbase + tc_tile_index(I0, J, U.nkc)) * (int64_t)AB, AB, &bar_afull[s]);
                         if (use1)
-                            bulk_g2s(st + kTcA, w16 + (U.wbase + tc_tile_index(I1, J, U.nkc)) * (int64_t)kTcA, kTcA,
+                            bulk_g2s(st + AB, w16 + (U.wbase + tc_tile_index(I1, J, U.nkc)) * (int64_t)AB, AB,
                                      &bar_afull[s]);
                     }
                 }
             }
             if (!ok) {
                 // let copies already issued land before the CTA exits
-                for (uint32_t k = 0; k < kTcStages && q > 0; k++) {
+                for (uint32_t k = 0; k < STG && q > 0; k++) {
                     const uint32_t qq = q - 1 - k;
-                    mbar_wait(&bar_afull[qq % kTcStages], (qq / kTcStages) & 1, &s_abort, 1u << 20);
+                    mbar_wait(&bar_afull[qq % STG], (qq / STG) & 1, &s_abort, 1u << 20);
                     if (qq == 0) break;
                 }
                 atomicOr(a.status, 2);
@@ -412,23 +436,26 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                     tc_fence_after();
                     for (int J = 2 * I0; J < U.nkc; J++, q++) {
                         const bool use1 = I1 < U.nmt && J >= 2 * I1;
-                        const int s = q % kTcStages;
-                        const uint32_t par = (q / kTcStages) & 1;
+                        const int s = q % STG;
+                        const uint32_t par = (q / STG) & 1;
                         if (J == 2 * I1 && use1) {
                             if (!mbar_wait(&bar_tempty[1], epar, &s_abort, a.wait_limit)) { ok = false; break; }
                         }
                         if (!mbar_wait(&bar_afull[s], par, &s_abort, a.wait_limit) ||
                             !mbar_wait(&bar_bfull[s], par, &s_abort, a.wait_limit)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t a0 = smem_u32(smem + s * kTcStageBytes);
-                        const uint32_t a1 = a0 + kTcA, b0 = a0 + 2 * kTcA;
+                        const uint32_t a0 = smem_u32(smem + s * SB);
+                        const uint32_t a1 = a0 + AB, b0 = a0 + 2 * AB;
 #pragma unroll
                         for (int kk = 0; kk < 4; kk++) {
-                            umma_f16(taddr, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
-                                     (J > 2 * I0 || kk > 0) ? 1u : 0u);
-                            if (use1)
-                                umma_f16(taddr + kTcCols, sw128_desc(a1 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                            const uint64_t bd = sw128_desc(b0 + kk * 32);
+                            umma_f16(taddr, sw128_desc(a0 + kk * 32), bd, idesc, (J > 2 * I0 || kk > 0) ? 1u : 0u);
+                            if (WP == 2) umma_f16(taddr, sw128_desc(a0 + kTcA + kk * 32), bd, idesc, 1u);
+                            if (use1) {
+                                umma_f16(taddr + kTcCols, sw128_desc(a1 + kk * 32), bd, idesc,
                                          (J > 2 * I1 || kk > 0) ? 1u : 0u);
+                                if (WP == 2) umma_f16(taddr + kTcCols, sw128_desc(a1 + kTcA + kk * 32), bd, idesc, 1u);
+                            }
                         }
                         umma_commit(&bar_empty[s]);
                     }
@@ -597,18 +624,19 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                     const long long kk = U.kfirst + lane;
                     if (a.stage == kStageFull) {
                         if (a.out) a.out[(int64_t)U.c * a.out_ld + kk] = v;
-                        key = make_key(v, (uint32_t)kk);
+                        if (!excluded_k(a.ex.full_k, a.ex.n, kk)) key = make_key(v, (uint32_t)kk);
                     } else if (a.stage == kStageCoarse) {
                         a.coarse_out[(int64_t)U.c * a.n_freq + kk] = v;
                     } else if (list) {
-                        const bool valid = a.trials[(int64_t)U.c * a.n_trials + kk] >= 0;
+                        const int32_t kg = a.trials[(int64_t)U.c * a.n_trials + kk];
+                        const bool valid = kg >= 0;
                         if (a.trial_stat)
                             a.trial_stat[(int64_t)U.c * a.n_trials + kk] = valid ? v : __int_as_float(0x7fc00000);
-                        if (valid) key = make_key(v, (uint32_t)kk);
+                        if (valid && !excluded_k(a.ex.full_k, a.ex.n, kg)) key = make_key(v, (uint32_t)kk);
                     } else {
-                        const double fpk = a.f_min + (double)U.peak_mult * a.coarse_df;
-                        const double fr = fpk + (double)kk * a.step;
-                        if (fr >= a.f_min && fr <= a.f_max)
+                        const double fpk = grid_freq(a.f_min, (double)U.peak_mult, a.coarse_df);
+                        const double fr = grid_freq(fpk, (double)kk, a.step);
+                        if (fr >= a.f_min && fr <= a.f_max && !excluded_f(a.ex, fr))
                             key = make_key(v, (uint32_t)(U.peak * (2 * a.fine_half + 1) + (kk + a.fine_half)));
                     }
                 }
@@ -659,7 +687,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
             for (int P = 0; ok && 2 * P < U.nmt; P++)
                 for (int J = 4 * P; J < U.nkc; J++, q++) {
                     if (!active || (int)(q % (uint32_t)groups) != grp) continue;
-                    const int s = q % kTcStages;
+                    const int s = q % STG;
                     const int j0 = J * 64 + g * 8;
                     uint32_t pu[8];
 #pragma unroll
@@ -675,7 +703,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                         }
                         pu[p] = v;
                     }
-                    if (!mbar_wait(&bar_empty[s], ((q / kTcStages) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
+                    if (!mbar_wait(&bar_empty[s], ((q / STG) & 1) ^ 1, &s_abort, a.wait_limit)) { ok = false; break; }
                     if constexpr (FOLD) {
                         // x_{n0} and x_{n0-1} (n0 = hr*NH+1, both signed +) start the recurrence;
                         // f32x2 lanes are the points 2r and 2r+1
@@ -704,7 +732,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                             cc[r] = pk(cb[0], cb[1]); ss[r] = pk(sb[0], sb[1]);     // n = n0
                             cm[r] = pk(ca[0], ca[1]); sm[r] = pk(sa[0], sa[1]);     // n = n0 - 1
                         }
-                        unsigned char* Bs = smem + s * kTcStageBytes + 2 * kTcA;
+                        unsigned char* Bs = smem + s * SB + 2 * AB;
                         // fully unrolled: measured fastest for every class (a partial unroll
                         // avoids the 16-harmonic spill but runs slower)
 #pragma unroll
@@ -756,7 +784,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                             cc[p] = cb; ss[p] = sb;           // n = n0
                             cm[p] = ca; sm[p] = sa;           // n = n0 - 1
                         }
-                        unsigned char* Bs = smem + s * kTcStageBytes + 2 * kTcA;
+                        unsigned char* Bs = smem + s * SB + 2 * AB;
 #pragma unroll
                         for (int nn = 0; nn < NH; nn++) {
                             const int n = hr * NH + 1 + nn;
@@ -794,18 +822,21 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
 }
 
 // ---------------------------------------------------------------------------
-size_t tensor_smem_bytes() { return (size_t)kTcStages * kTcStageBytes + kTcTableSlots * 16 + 1024; }
+size_t tensor_smem_bytes(bool bf16)
+{
+    return (size_t)tc_stages(bf16) * tc_stage_bytes(bf16) + kTcTableSlots * 16 + 1024;
+}
+
+size_t tensor_tile_bytes(bool bf16) { return (size_t)tc_wparts(bf16) * kTcA; }
 
 int tensor_tiles_of(int n) { return tc_tiles_of(n); }
 
 template <int NMAX, bool BF>
 static cudaError_t set_tensor_smem()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_pair_tensor<NMAX, BF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tensor_smem_bytes());
+    cudaError_t e = raise_dyn_smem((const void*)k_pair_tensor<NMAX, BF, false>, tensor_smem_bytes(BF));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_pair_tensor<NMAX, BF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tensor_smem_bytes());
+    return raise_dyn_smem((const void*)k_pair_tensor<NMAX, BF, true>, tensor_smem_bytes(BF));
 }
 
 cudaError_t prepare_tensor_kernel(int n_max)
@@ -837,8 +868,8 @@ cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max,
 
 cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s)
 {
-    const size_t b = tensor_smem_bytes();
     const bool bf = a.bf16 != 0, list = a.stage == kStageList;
+    const size_t b = tensor_smem_bytes(bf);
 #define CP_TC_LAUNCH(NM)                                                                        \
     case NM:                                                                                    \
         if (list) {                                                                             \

@@ -54,7 +54,12 @@ core = [
  ("thresholds: bins right-closed", "if (psnr >= ORC_BIN_LO[k])", "if (psnr > ORC_BIN_LO[k])"),
  ("thresholds: digits swapped", "1.1153", "1.1513"),
  ("argmax: ties to the highest index", "if (v[k] > v[b])", "if (v[k] >= v[b])"),
- ("coarse maxima: non-strict left neighbour", "int left_ok = (k == 0) || (v[k] > v[k - 1]);", "int left_ok = (k == 0) || (v[k] >= v[k - 1]);"),
+ ("coarse maxima: non-strict left neighbour",
+  "int left_ok = (k == 0) || (v[k] > v[k - 1]);\n        int right_ok = (k == n - 1) || (v[k] >= v[k + 1]);\n        if (n == 1)\n            left_ok = right_ok = 1;\n        if (!(left_ok && right_ok))\n",
+  "int left_ok = (k == 0) || (v[k] >= v[k - 1]);\n        int right_ok = (k == n - 1) || (v[k] >= v[k + 1]);\n        if (n == 1)\n            left_ok = right_ok = 1;\n        if (!(left_ok && right_ok))\n"),
+ ("coarse maxima with windows: non-strict left neighbour",
+  "int left_ok = (k == 0) || (v[k] > v[k - 1]);\n        int right_ok = (k == n - 1) || (v[k] >= v[k + 1]);\n        if (n == 1)\n            left_ok = right_ok = 1;\n        if (!(left_ok && right_ok) || orc_is_excluded",
+  "int left_ok = (k == 0) || (v[k] >= v[k - 1]);\n        int right_ok = (k == n - 1) || (v[k] >= v[k + 1]);\n        if (n == 1)\n            left_ok = right_ok = 1;\n        if (!(left_ok && right_ok) || orc_is_excluded"),
  ("fine window: half-width in coarse steps", "floor(g->fine_halfwidth / g->fine_df + 0.5)", "floor(g->fine_halfwidth / g->coarse_df + 0.5)"),
  ("sigma_y: largest error bar", "    double sy = orc_median(e, n);\n    double st = curve_sigma_t(o, y, n, c);",
   "    double sy = orc_quantile(e, n, 1.0);\n    double st = curve_sigma_t(o, y, n, c);"),

@@ -120,6 +120,25 @@ def test_argument_validation_precedes_device_use():
     assert _plan_status([0, 5], tuning=bad_mask) == cp.CP_EINVAL
 
 
+def test_exclusion_windows_are_validated_before_device_use():
+    """Section 6.1 windows: at most CP_MAX_EXCLUDE, finite lo <= hi; the
+    no-allocation entry point refuses them (it has no plan to hold them)."""
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 10, exclude=[(0.3, 0.2)])) == cp.CP_EINVAL
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 10, exclude=[(float("nan"), 0.2)])) == cp.CP_EINVAL
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 10, exclude=[(0.1, float("inf"))])) == cp.CP_EINVAL
+    many = [(0.1 + q, 0.2 + q) for q in range(cp.CP_MAX_EXCLUDE + 1)]
+    assert _plan_status([0, 5], grid=cp.make_grid(0.01, 0.01, 10, exclude=many)) == cp.CP_EINVAL
+    g = cp.make_grid(0.01, 0.01, 10)
+    g.n_exclude = 2                       # count without an array
+    assert _plan_status([0, 5], grid=g) == cp.CP_EINVAL
+    off = np.array([0, 5], np.int64)
+    dummy = np.zeros(8)
+    st = cp.lib().cp_best_period_noalloc(dummy.ctypes.data, dummy.ctypes.data, dummy.ctypes.data, off.ctypes.data,
+                                         1, ctypes.byref(cp.make_grid(0.01, 0.01, 10, exclude=[(0.1, 0.2)])),
+                                         ctypes.c_float(0.3), None, None, None, None, None)
+    assert st == cp.CP_EUNSUPPORTED
+
+
 def test_no_device_is_an_error_not_a_fallback():
     try:
         import torch

@@ -3,8 +3,10 @@ against the FP64 oracle of Eq. (CKP).
 
 Bar: per curve max_k |nCKP_gpu - nCKP_oracle| / max_k |nCKP_oracle| <= 1e-3
 for FP16 operands with enough harmonics for the curve's sigma_t; the best
-index is accepted at the same tolerance (c16 reading).  BF16 operands carry
-8 mantissa bits, so their error is reported against a looser bound.
+index is accepted at the same tolerance (c16 reading).  BF16 operands: the
+magnitude-kernel operand is split into two BF16 parts (hi + lo), so its
+rounding no longer counts; the Z operand's single BF16 rounding (8
+significand bits) leaves a floor near 1e-3, held here to BF16_TOL = 2e-3.
 """
 import os
 
@@ -20,6 +22,7 @@ pytestmark = pytest.mark.gpu
 import paper_1412_1840_gb300 as cp  # noqa: E402
 
 TOL = 1e-3
+BF16_TOL = 2e-3   # measured worst case 1.5e-3 (one curve, 32 harmonics); FP16 meets TOL
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -80,11 +83,42 @@ def test_tensor_truncation_converges_with_n_max(ragged):
     assert errs[16] <= TOL
 
 
-def test_tensor_bf16_error_bound(ragged):
+@pytest.mark.parametrize("n_max", [12, 16, 32])
+def test_tensor_bf16_parity_ragged(ragged, n_max):
+    """BF16 operands: W' as hi + lo BF16 parts (two MMAs per K slice), Z in
+    one BF16 part."""
     b, g, ref = ragged
-    out, best, _ = run(b, g, sigma_t=0.45, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_BF16, n_max=16)
-    err = peak_err(out, ref, range(b.n_curves))
-    assert np.all(err <= 3e-2), err          # 8-bit mantissa: ~8x the FP16 error
+    out, best, _ = run(b, g, sigma_t=0.45, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_BF16, n_max=n_max)
+    rows = range(b.n_curves)
+    err = peak_err(out, ref, rows)
+    print("\nBF16, %d harmonics: per-curve peak-relative error" % n_max, " ".join("%.2e" % x for x in err))
+    assert np.all(err <= BF16_TOL), err
+    accept_best(best, ref, rows, BF16_TOL)
+
+
+def test_tensor_bf16_edge_batch_and_hierarchical():
+    b = synth.edge_batch()
+    g = synth.Grid(0.005, 0.005, 600)
+    out, best, _ = run(b, g, sigma_t=0.3, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_BF16, n_max=16)
+    ref = oracle.batch_nckp(b, np.full(b.n_curves, float(np.float32(0.3))), g.freqs())
+    rows = [c for c in range(b.n_curves) if c != 3]
+    assert np.all(out[3] == 0.0)
+    err = peak_err(out, ref, rows)
+    assert np.all(err <= BF16_TOL), err
+    accept_best(best, ref, rows, BF16_TOL)
+    b = synth.ragged_batch(6, seed=24, n_lo=100, n_hi=260, span=1200.0)
+    g = synth.Grid(0.01, 1e-4, 19901, hierarchical=True, coarse_df=4e-3, top_k=10, fine_df=1e-4,
+                   fine_halfwidth=4e-3)
+    with cp.Plan(b.times, b.mags, b.errs, b.offsets, cp.grid_from(g), sigma_t=0.35, form=cp.CP_FORM_TENSOR,
+                 dtype=cp.CP_DTYPE_BF16, n_max=16) as p:
+        hb = p.best_period()
+    st = float(np.float32(0.35))
+    ref = oracle.batch_best(b, g, sigma_t=st)
+    for c in range(b.n_curves):
+        t, m, e = b.curve(c)
+        v = oracle.nckp(t, m.astype(np.float64), oracle.median(e.astype(np.float64)), st, [hb["best_freq"][c]])[0]
+        vstar = ref["best_stat"][c]
+        assert v >= vstar - BF16_TOL * abs(vstar) and abs(hb["best_stat"][c] - v) <= BF16_TOL * abs(vstar)
 
 
 def test_tensor_edge_batch():
@@ -216,10 +250,11 @@ def test_error_matrix_on_benchmark_curves():
         print("  %-12s n_max %-3s %.2e" % (k[0], k[1], v))
     assert table[("fp16", 0)] <= TOL
     assert table[("fp32 direct", "-")] <= 1e-5
-    assert table[("bf16", 0)] <= 3e-2
+    assert table[("bf16", 0)] <= BF16_TOL
 
 
-def test_full_size_tensor_form_sampled():
+@pytest.mark.parametrize("dtype", [cp.CP_DTYPE_FP16, cp.CP_DTYPE_BF16])
+def test_full_size_tensor_form_sampled(dtype):
     """The 4096-curve, 49,981-frequency benchmark batch in the benchmark's
     tensor-form launch configuration (device inputs, sigma_t rule, per-curve
     harmonics, the GB300 tuning table): sampled periodogram values of six
@@ -232,7 +267,7 @@ def test_full_size_tensor_form_sampled():
     rng = np.random.default_rng(97)
     curves = np.sort(rng.choice(b.n_curves, 6, replace=False))
     with cp.Plan(td, md, ed, b.offsets, cp.grid_from(g), sigma_t_mode=cp.CP_SIGMA_T_RULE,
-                 form=cp.CP_FORM_TENSOR, n_max=0, tuning=table) as p:
+                 form=cp.CP_FORM_TENSOR, n_max=0, dtype=dtype, tuning=table) as p:
         best = p.best_period()
         out = torch.empty((b.n_curves, g.n_freq), dtype=torch.float32, device="cuda")
         p.periodogram(out)
@@ -252,4 +287,54 @@ def test_full_size_tensor_form_sampled():
         ref = oracle.nckp(t, m.astype(np.float64), oracle.median(e.astype(np.float64)),
                           float(stats["sigma_t"][c]), f[ks])
         peak = max(abs(ref).max(), abs(rows[r]).max())
-        assert np.max(np.abs(rows[r][ks] - ref)) <= TOL * peak, c
+        assert np.max(np.abs(rows[r][ks] - ref)) <= (TOL if dtype == cp.CP_DTYPE_FP16 else BF16_TOL) * peak, c
+
+
+def test_rule_mode_plan_follows_changed_magnitudes():
+    """Per-curve harmonic counts in the rule mode follow the magnitudes bound
+    to the plan.  (1) cp_whiten rewrites the bound device buffer; the next
+    search matches the oracle on the whitened magnitudes.  (2) One curve's
+    magnitudes become strongly skewed (sigma_t drops from ~0.6, 8 harmonics,
+    to ~0.15, which needs 32): the call re-plans on the device-computed
+    sigma_t and still meets 1e-3; so does the periodogram pass through cp_sync."""
+    b = synth.ragged_batch(6, seed=81, n_lo=200, n_hi=400, span=1500.0)
+    g = synth.Grid(0.01, 7e-4, 700)
+    td = torch.from_numpy(b.times).cuda()
+    md = torch.from_numpy(b.mags.copy()).cuda()
+    ed = torch.from_numpy(b.errs).cuda()
+
+    def check(p, mags):
+        cur = synth.Batch(b.times, mags, b.errs, b.offsets, b.period, b.periodic, b.kind)
+        st = oracle.curve_stats(cur, sigma_t_mode=2)["sigma_t"].astype(np.float32).astype(np.float64)
+        ref = oracle.batch_nckp(cur, st, g.freqs())
+        best = p.best_period()
+        out = torch.empty((b.n_curves, g.n_freq), dtype=torch.float32, device="cuda")
+        p.periodogram(out)
+        p.sync()
+        got = out.cpu().numpy()
+        rows = range(b.n_curves)
+        assert np.all(peak_err(got, ref, rows) <= TOL), peak_err(got, ref, rows)
+        accept_best(best, ref, rows, TOL)
+        np.testing.assert_allclose(p.curve_stats()["sigma_t"], st, rtol=2e-7, atol=0)
+        return best
+
+    with cp.Plan(td, md, ed, b.offsets, cp.grid_from(g), sigma_t_mode=cp.CP_SIGMA_T_RULE, form=cp.CP_FORM_TENSOR,
+                 n_max=0) as p:
+        best = check(p, b.mags)
+        classes0 = p.info()["class_curves"]
+        # (1) whiten in place at the found periods
+        p0 = 1.0 / best["best_freq"]
+        cp.cp_whiten(td, md, b.offsets, p0, out=md)
+        torch.cuda.synchronize()
+        check(p, md.cpu().numpy())
+        # (2) a strongly skewed curve 0 (log-normal magnitudes)
+        rng = np.random.default_rng(5)
+        n0 = int(b.offsets[1])
+        skewed = (17.0 + np.exp(rng.normal(0.0, 1.5, n0))).astype(np.float32)
+        md[:n0] = torch.from_numpy(skewed).cuda()
+        torch.cuda.synchronize()
+        replans0 = p.info()["replans"]
+        check(p, md.cpu().numpy())
+        info = p.info()
+        assert info["replans"] >= replans0 + 1
+        assert info["class_curves"] != classes0
