@@ -62,8 +62,9 @@ def _brute_top_maxima(v, f, top_k, ex):
 
 def test_coarse_peaks_skip_excluded_candidates_by_brute_force():
     rng = np.random.default_rng(62)
-    for trial in range(20):
-        v = np.round(rng.normal(size=120), 1)          # ties and plateaus
+    for trial in range(40):
+        # ties and plateaus, also among the highest values
+        v = np.round(rng.normal(size=120), 1) if trial % 2 else rng.integers(0, 5, size=120).astype(np.float64)
         f = 0.1 + np.arange(120) * 0.01
         ex = ((f[5], f[9]), (f[60] - 1e-9, f[60] + 1e-9), (2.0, 3.0))
         got = oracle.top_local_maxima_excl(v, 7, 0.1, 0.01, ex)
