@@ -548,6 +548,9 @@ def main():
         rel = np.abs(res["tensor"].astype(np.float64) - res["direct"]) / \
             np.maximum(np.abs(res["direct"].astype(np.float64)), 1e-30)
         thr["tensor_best_stat_max_rel_diff_vs_direct"] = float(rel.max())
+        # the coarse top-10 cutoff can rank near-tied peaks differently within 1e-3, and then the two
+        # forms refine different peaks: per-curve agreement is the fraction, the oracle test the bar
+        thr["tensor_best_stat_within_1e-3_of_direct_frac"] = float(np.mean(rel <= 1e-3))
         thr["agreement_with_oracle"] = "tests/test_gpu_agreement.py: fixed 1,000-curve sample of this generator"
         del ttd, tmd, ted
 
