@@ -91,7 +91,7 @@ enum { CP_MEM_HOST = 0, CP_MEM_DEVICE = 1 };
  * and every ordering that lies within the FP32 error bound is decided again
  * from FP64 window values (exact 64-bit phases), and a band whose candidate
  * set the bound cannot prove complete is scanned in FP64 over the whole grid,
- * so the lists are those of an FP64 evaluation (n_freq < 2^29).
+ * so the lists are those of an FP64 evaluation (n_freq < 2^28).
  * nCKP is then evaluated at the n_bands * trials_per_band trial grid
  * frequencies only, and the best is the largest, ties to the lower
  * position in the band-major trial list.  best_idx is the winning grid

@@ -840,8 +840,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             return fail(CP_EINVAL, "cp_plan: n_bands must be in [1, 10]");
         if (g.trials_per_band < 1 || g.trials_per_band > kBandsMaxTrials)
             return fail(CP_EINVAL, "cp_plan: trials_per_band must be in [1, " + std::to_string(kBandsMaxTrials) + "]");
-        if (g.n_freq >= ((int64_t)1 << 29))
-            return fail(CP_EUNSUPPORTED, "cp_plan: the bands method supports grids of fewer than 2^29 points");
+        if (g.n_freq >= ((int64_t)1 << 28))
+            return fail(CP_EUNSUPPORTED, "cp_plan: the bands method supports grids of fewer than 2^28 points");
         p->bands = true;
         p->n_trials = g.n_bands * g.trials_per_band;
         // grid indices of the one-day frequencies |1/f - 1| < 1e-4 (a contiguous range; the

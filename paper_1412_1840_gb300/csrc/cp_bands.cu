@@ -39,11 +39,26 @@ constexpr int kWinThreads = 256;
 constexpr int kWinRun = 16;                    // frequencies per thread per pass (stride kWinThreads)
 constexpr int kWinHalf = kWinRun / 2;          // q and q + kWinHalf share an f32x2 register
 constexpr int kWinSeg = 2 * kWinThreads * kWinRun - 2;   // grid points per segment (two passes with neighbours)
-// |S_fp32 - S_exact| <= kWinErr m^2 for a band of m > 1 samples: each term
-// exp(i x) carries the SFU sincos error (< 2^-20.5 absolute) plus at most 15
-// FP32 rotations (~2^-23 each), and |S| <= m^2; the bound leaves a margin of
-// about two.  Bands of one sample are exact (S = 1).
-constexpr float kWinErr = 2e-5f;
+// Error bound of an FP32 window value S of a band of m > 1 samples: each term
+// exp(i x) carries at most kWinTermErr absolute error (SFU sin/cos below
+// 2^-20.5 on an FP32 argument, plus up to 15 FP32 rotations of ~2^-22 each,
+// about 4e-6 together, taken with a margin) and the m-term sums add
+// at most m 2^-24 each, so |Z_fp32 - Z| <= e = m (kWinTermErr + m 2^-24) and
+// |S_fp32 - S| <= 2 (sqrt(S_fp32) + e) e + e^2, plus the rounding of |Z|^2.
+// The bound grows with the value: small side lobes are decided far more tightly
+// than a bound on the band's largest possible value m^2.  Bands of one sample
+// are exact (S = 1).
+constexpr float kWinTermErr = 6e-6f;
+__device__ __forceinline__ float win_err(float v, float e)
+{
+    if (e <= 0.f) return 0.f;
+    const float z = sqrtf(fmaxf(v, 0.f)) + e;
+    return fmaf(2.f * z, e, e * e) + fabsf(v) * 2.4e-7f;
+}
+__device__ __forceinline__ float win_term_err(int m)
+{
+    return m <= 1 ? 0.f : (float)m * (kWinTermErr + (float)m * 5.96e-8f);
+}
 __host__ __device__ constexpr int win_candidates(int n_t) { return 2 * n_t; }
 
 // ===========================================================================
@@ -174,12 +189,13 @@ __host__ __device__ inline WinLayout win_layout(int max_band_points, int n_t)
 }
 
 // Candidate key: the FP32 window value, then bit 31 set when the point's
-// local-maximum test is certain (both comparisons decided by more than e2),
-// then the lower grid index k.
-__device__ __forceinline__ unsigned long long win_key(const float* S, int x, int k, int K, float e2)
+// local-maximum test is certain (both comparisons decided by more than the two
+// values' error bounds), then the lower grid index k.
+__device__ __forceinline__ unsigned long long win_key(const float* S, int x, int k, int K, float e)
 {
-    const float v = S[x];
-    const bool sure = (k == 0 || v > S[x - 1] + e2) && (k == K - 1 || v > S[x + 1] + e2);
+    const float v = S[x], ev = win_err(v, e);
+    const bool sure = (k == 0 || v - S[x - 1] > ev + win_err(S[x - 1], e)) &&
+                      (k == K - 1 || v - S[x + 1] > ev + win_err(S[x + 1], e));
     return ((unsigned long long)orderable(v) << 32) | (sure ? 0x80000000ull : 0ull) |
            (unsigned long long)(0x7fffffffu - (uint32_t)k);
 }
@@ -275,8 +291,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
         __syncthreads();
     }
     const int m = min(s_m, a.max_band_points);
-    // two error bounds apart: a comparison decided by more is the same in exact arithmetic
-    const float e2 = m <= 1 ? 0.f : 2.f * kWinErr * (float)m * (float)m;
+    const float e2 = win_term_err(m);   // per-term error scale of the band's window values
 
     unsigned long long* run = run0;   // running list: the n_t highest so far, descending
     unsigned long long* nxt = run1;
@@ -348,8 +363,11 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
             if (j < len) {
                 const int x = k - v0;
                 const float v = S[x];
-                const bool lok = k == 0 || (e2 > 0.f ? v >= S[x - 1] - e2 : v > S[x - 1]);
-                const bool rok = k == K - 1 || v >= S[x + 1] - e2;
+                // may be a local maximum in exact values: not decided against it by more
+                // than the two values' error bounds (exact bands: the exact test)
+                const float ev = win_err(v, e2);
+                const bool lok = k == 0 || (e2 > 0.f ? v >= S[x - 1] - ev - win_err(S[x - 1], e2) : v > S[x - 1]);
+                const bool rok = k == K - 1 || v >= S[x + 1] - ev - win_err(S[x + 1], e2);
                 ok = lok && rok && !(k >= a.ex_lo && k <= a.ex_hi) && win_key(S, x, k, K, e2) > floor_key;
             }
             const uint32_t bal = __ballot_sync(0xffffffffu, ok);
@@ -555,7 +573,8 @@ __global__ void __launch_bounds__(32 * kRefineWarps) k_window_refine(const Windo
     const int K = a.n_freq, n_t = a.n_t, nc = win_candidates(n_t);
     ulonglong2* pts = reinterpret_cast<ulonglong2*>(smem) + (size_t)warp * a.max_band_points;
     // per candidate: value (FP32 from the window, or FP64 where recomputed) and the grid
-    // index with flags (bit 30: local-maximum test uncertain, bit 29: recompute)
+    // index (bits 0-27) with flags: bit 30 local-maximum test uncertain, bit 29
+    // recompute, bit 28 the value is exact
     unsigned char* vbase = smem + (size_t)kRefineWarps * a.max_band_points * sizeof(ulonglong2);
     double* val = reinterpret_cast<double*>(vbase) + (size_t)warp * nc;
     int32_t* kk = reinterpret_cast<int32_t*>(vbase + (size_t)kRefineWarps * nc * sizeof(double)) + (size_t)warp * nc;
@@ -575,7 +594,7 @@ __global__ void __launch_bounds__(32 * kRefineWarps) k_window_refine(const Windo
     }
     m = min(m, a.max_band_points);
     __syncwarp();
-    const float dl = m <= 1 ? 0.f : kWinErr * (float)m * (float)m;   // |S_fp32 - S| bound
+    const float e = win_term_err(m);               // per-term error scale: win_err(v, e) bounds |S_fp32 - S|
 
     // candidates (descending FP32 value, then sure-first, then lower k)
     const unsigned long long* cand = a.cand + (int64_t)job * nc;
@@ -594,19 +613,38 @@ __global__ void __launch_bounds__(32 * kRefineWarps) k_window_refine(const Windo
     const float last32 = cnt > 0 ? (float)val[cnt - 1] : 0.f;
     const bool full = cnt == nc;
 
-    // which candidates need the exact value: an uncertain local-maximum test, or a
-    // neighbour in the list closer than two error bounds (order undecided)
-    for (int r = lane; r < cnt; r += 32) {
+    // Only candidates that can still reach the first n_t trials matter: with the n_t
+    // certain maxima of the list bounding the n_t-th trial's value from below by L,
+    // a candidate whose value is below L by more than its error bound cannot.
+    int rel = cnt;
+    if (lane == 0) {
+        int secured = 0;
+        double L = INFINITY;
+        for (int r = 0; r < cnt; r++) {
+            const float v = (float)val[r];
+            if (secured >= n_t && (double)v + (double)win_err(v, e) < L) { rel = r; break; }
+            if (!(kk[r] & 0x40000000) && secured < n_t) {
+                secured++;
+                L = fmin(L, (double)v - (double)win_err(v, e));
+            }
+        }
+    }
+    rel = __shfl_sync(0xffffffffu, rel, 0);
+
+    // which of them need the exact value: an uncertain local-maximum test, or a
+    // neighbour in the list closer than the two values' error bounds (order undecided)
+    for (int r = lane; r < rel; r += 32) {
         const bool unsure = (kk[r] & 0x40000000) != 0;
-        const double v = val[r];
-        const bool close = (r > 0 && val[r - 1] - v <= 2.0 * dl) || (r + 1 < cnt && v - val[r + 1] <= 2.0 * dl);
+        const float v = (float)val[r], ev = win_err(v, e);
+        const bool close = (r > 0 && val[r - 1] - val[r] <= (double)(ev + win_err((float)val[r - 1], e))) ||
+                           (r + 1 < cnt && val[r] - val[r + 1] <= (double)(ev + win_err((float)val[r + 1], e)));
         if (unsure || close) kk[r] |= 0x20000000;
     }
     __syncwarp();
-    for (int r = 0; r < cnt; r++) {
+    for (int r = 0; r < rel; r++) {
         const int tag = kk[r];
         if (!(tag & 0x20000000)) continue;
-        const int k = tag & 0x1fffffff;
+        const int k = tag & 0x0fffffff;
         const double sk = window_fp64(pts, m, (uint64_t)k, lane);
         bool keep = true;
         if (tag & 0x40000000) {     // the local-maximum test in exact values
@@ -615,7 +653,7 @@ __global__ void __launch_bounds__(32 * kRefineWarps) k_window_refine(const Windo
         }
         if (lane == 0) {
             val[r] = sk;
-            if (!keep) kk[r] = -1;
+            kk[r] = keep ? (kk[r] | 0x10000000) : -1;   // bit 28: the value is exact
         }
         __syncwarp();
     }
@@ -626,26 +664,31 @@ __global__ void __launch_bounds__(32 * kRefineWarps) k_window_refine(const Windo
     int scan = 0;
     if (lane == 0) {
         int kept = 0;
-        for (int r = 0; r < cnt; r++) {
+        for (int r = 0; r < rel; r++) {
             if (kk[r] < 0) continue;
             const double v = val[r];
-            const int k = kk[r] & 0x1fffffff;
+            const int k = kk[r] & 0x0fffffff;
+            const int tagged = k | (kk[r] & 0x10000000);   // keep the exact-value flag
             int q = kept;
-            while (q > 0 && (val[q - 1] < v || (val[q - 1] == v && (kk[q - 1] & 0x1fffffff) > k))) {
+            while (q > 0 && (val[q - 1] < v || (val[q - 1] == v && (kk[q - 1] & 0x0fffffff) > k))) {
                 val[q] = val[q - 1];
                 kk[q] = kk[q - 1];
                 q--;
             }
             val[q] = v;
-            kk[q] = k;
+            kk[q] = tagged;
             kept++;
         }
-        for (int r = 0; r < n_t; r++) out[r] = r < kept ? (kk[r] & 0x1fffffff) : -1;
+        for (int r = 0; r < n_t; r++) out[r] = r < kept ? (kk[r] & 0x0fffffff) : -1;
         // a full candidate list leaves out points whose FP32 value is below its last
         // entry: they cannot reach the trials when the n_t-th trial lies above it by
-        // more than two error bounds; otherwise (peaks of nearly equal height, such
+        // more than both error bounds; otherwise (peaks of nearly equal height, such
         // as the maxima 4 of a two-sample band) the band is scanned exactly
-        scan = full && (kept < n_t || val[n_t - 1] - (double)dl <= (double)last32 + (double)dl);
+        if (full) {
+            const double vt = kept >= n_t ? val[n_t - 1] : 0.0;
+            const double et = kept >= n_t && !(kk[n_t - 1] & 0x10000000) ? (double)win_err((float)vt, e) : 0.0;
+            scan = kept < n_t || vt - et <= (double)last32 + (double)win_err(last32, e);
+        }
     }
     scan = __shfl_sync(0xffffffffu, scan, 0);
     if (!scan) return;
