@@ -532,6 +532,43 @@ __device__ double window_fp64(const ulonglong2* pts, int m, uint64_t k, int lane
     return re * re + im * im;
 }
 
+// A tighter, still cheap evaluation (FP32): cos and sin of each term from the
+// Taylor polynomials on the exactly reduced angle (each below 2.5e-7 absolute
+// error with the FP32 rounding of the evaluation and of the angle), compensated
+// (Kahan) sums per lane (below 2 2^-24 per term), lanes combined in FP64.  So
+// |Z_acc - Z| <= e1 = m kAccTermErr, taken with a margin, and
+// |S_acc - S| <= 2 (|Z_acc| + e1) e1 + e1^2.
+constexpr float kAccTermErr = 1e-6f;
+__device__ double window_acc(const ulonglong2* pts, int m, uint64_t k, int lane, float& bound)
+{
+    bound = 0.f;
+    if (m <= 1) return (double)m;
+    float re = 0.f, im = 0.f, cr = 0.f, ci = 0.f;
+    for (int p = lane; p < m; p += 32) {
+        const uint64_t U = pts[p].x + k * pts[p].y;
+        float sv, cv;
+        sincos2pi_turns((uint32_t)(U >> 32), sv, cv);
+        float y = cv - cr, t = re + y;
+        cr = (t - re) - y;
+        re = t;
+        y = sv - ci;
+        t = im + y;
+        ci = (t - im) - y;
+        im = t;
+    }
+    double R = (double)re - (double)cr, I = (double)im - (double)ci;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        R += __shfl_xor_sync(0xffffffffu, R, o);
+        I += __shfl_xor_sync(0xffffffffu, I, o);
+    }
+    const double S = R * R + I * I;
+    const float e1 = (float)m * kAccTermErr;
+    const float z = sqrtf((float)S) + e1;
+    bound = fmaf(2.f * z, e1, e1 * e1);
+    return S;
+}
+
 // The same value computed by one lane alone (points in sample order).
 __device__ double window_fp64_lane(const ulonglong2* pts, int m, uint64_t k)
 {
@@ -563,7 +600,7 @@ __device__ __forceinline__ void list_insert(double* val, int32_t* kk, int& cnt, 
     if (cnt < n_t) cnt++;
 }
 
-__global__ void __launch_bounds__(32 * kRefineWarps) k_window_refine(const WindowArgs a)
+__global__ void __launch_bounds__(32 * kRefineWarps, 2) k_window_refine(const WindowArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -572,12 +609,15 @@ __global__ void __launch_bounds__(32 * kRefineWarps) k_window_refine(const Windo
     const int c = job / a.n_bands, b = job - c * a.n_bands;
     const int K = a.n_freq, n_t = a.n_t, nc = win_candidates(n_t);
     ulonglong2* pts = reinterpret_cast<ulonglong2*>(smem) + (size_t)warp * a.max_band_points;
-    // per candidate: value (FP32 from the window, or FP64 where recomputed) and the grid
-    // index (bits 0-27) with flags: bit 30 local-maximum test uncertain, bit 29
-    // recompute, bit 28 the value is exact
+    // per candidate: value (FP32 from the window, accurate FP32 or FP64 where
+    // recomputed), its error bound, and the grid index (bits 0-27) with flags:
+    // bit 30 local-maximum test uncertain, bit 29 open, bit 28 the value is exact
     unsigned char* vbase = smem + (size_t)kRefineWarps * a.max_band_points * sizeof(ulonglong2);
     double* val = reinterpret_cast<double*>(vbase) + (size_t)warp * nc;
     int32_t* kk = reinterpret_cast<int32_t*>(vbase + (size_t)kRefineWarps * nc * sizeof(double)) + (size_t)warp * nc;
+    float* eb = reinterpret_cast<float*>(vbase + (size_t)kRefineWarps * nc * (sizeof(double) + sizeof(int32_t))) +
+                (size_t)warp * nc;   // error bound of each value (0 once exact)
+    float* fv = eb + (size_t)kRefineWarps * nc;   // each value rounded to FP32 (FP64 arithmetic is slow here)
     const int64_t off = a.cp[c].off;
     const int n = a.cp[c].n;
     const int band = a.kept[(int64_t)c * a.n_bands + b];
@@ -603,93 +643,155 @@ __global__ void __launch_bounds__(32 * kRefineWarps) k_window_refine(const Windo
         const int r = r0 + lane;
         const unsigned long long key = r < nc ? cand[r] : 0ull;
         if (key) {
-            val[r] = (double)from_orderable((uint32_t)(key >> 32));
+            fv[r] = from_orderable((uint32_t)(key >> 32));
+            val[r] = (double)fv[r];
             kk[r] = (int32_t)(0x7fffffffu - (uint32_t)(key & 0x7fffffffu)) | (int32_t)((key & 0x80000000ull) ? 0 : 0x40000000);
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, key != 0ull);
         cnt += __popc(bal);
     }
     __syncwarp();
-    const float last32 = cnt > 0 ? (float)val[cnt - 1] : 0.f;
+    const float last32 = cnt > 0 ? fv[cnt - 1] : 0.f;
     const bool full = cnt == nc;
 
     // Only candidates that can still reach the first n_t trials matter: with the n_t
     // certain maxima of the list bounding the n_t-th trial's value from below by L,
     // a candidate whose value is below L by more than its error bound cannot.
     int rel = cnt;
-    if (lane == 0) {
+    if (lane == 0) {                               // FP32 with directed rounding: the cut errs on the safe side
         int secured = 0;
-        double L = INFINITY;
+        float L = INFINITY;
         for (int r = 0; r < cnt; r++) {
-            const float v = (float)val[r];
-            if (secured >= n_t && (double)v + (double)win_err(v, e) < L) { rel = r; break; }
+            const float v = fv[r], er = win_err(v, e);
+            if (secured >= n_t && __fadd_ru(v, er) < L) { rel = r; break; }
             if (!(kk[r] & 0x40000000) && secured < n_t) {
                 secured++;
-                L = fmin(L, (double)v - (double)win_err(v, e));
+                L = fminf(L, __fsub_rd(v, er));
             }
         }
     }
     rel = __shfl_sync(0xffffffffu, rel, 0);
 
-    // which of them need the exact value: an uncertain local-maximum test, or a
-    // neighbour in the list closer than the two values' error bounds (order undecided)
-    for (int r = lane; r < rel; r += 32) {
-        const bool unsure = (kk[r] & 0x40000000) != 0;
-        const float v = (float)val[r], ev = win_err(v, e);
-        const bool close = (r > 0 && val[r - 1] - val[r] <= (double)(ev + win_err((float)val[r - 1], e))) ||
-                           (r + 1 < cnt && val[r] - val[r + 1] <= (double)(ev + win_err((float)val[r + 1], e)));
-        if (unsure || close) kk[r] |= 0x20000000;
-    }
+    // Decide what the FP32 bounds leave open: first with the accurate FP32 value
+    // (a bound about ten times tighter), then in FP64, repeated until nothing is
+    // open.  Each round sorts the live entries (value descending, ties to the
+    // lower k) and opens an entry whose local-maximum test is uncertain, or whose
+    // interval value +- bound meets that of another entry when one of the two
+    // sits in the first n_t places (their order, or which of them is a trial, is
+    // undecided).  With nothing open, every entry outside the first n_t lies
+    // below each of them and the first n_t are in their true order.
+    for (int r = lane; r < rel; r += 32) eb[r] = win_err(fv[r], e);
     __syncwarp();
-    for (int r = 0; r < rel; r++) {
-        const int tag = kk[r];
-        if (!(tag & 0x20000000)) continue;
-        const int k = tag & 0x0fffffff;
-        const double sk = window_fp64(pts, m, (uint64_t)k, lane);
-        bool keep = true;
-        if (tag & 0x40000000) {     // the local-maximum test in exact values
-            if (k > 0) keep = sk > window_fp64(pts, m, (uint64_t)(k - 1), lane);
-            if (keep && k < K - 1) keep = sk >= window_fp64(pts, m, (uint64_t)(k + 1), lane);
+    for (int tier = 1;; tier = 2) {
+        if (lane == 0) {                           // drop the rejected entries, sort the rest
+            int kept = 0;                          // (values >= 0: their bit patterns order as integers)
+            for (int r = 0; r < rel; r++) {
+                const int t = kk[r];
+                if (t < 0) continue;
+                const double v = val[r];
+                const long long vb = __double_as_longlong(v);
+                const float bv = eb[r], f = fv[r];
+                const int k = t & 0x0fffffff;
+                int q = kept;
+                while (q > 0) {
+                    const long long pb = __double_as_longlong(val[q - 1]);
+                    if (!(pb < vb || (pb == vb && (kk[q - 1] & 0x0fffffff) > k))) break;
+                    val[q] = val[q - 1];
+                    eb[q] = eb[q - 1];
+                    fv[q] = fv[q - 1];
+                    kk[q] = kk[q - 1];
+                    q--;
+                }
+                val[q] = v;
+                eb[q] = bv;
+                fv[q] = f;
+                kk[q] = t;
+                kept++;
+            }
+            rel = kept;
         }
-        if (lane == 0) {
-            val[r] = sk;
-            kk[r] = keep ? (kk[r] | 0x10000000) : -1;   // bit 28: the value is exact
+        rel = __shfl_sync(0xffffffffu, rel, 0);
+        __syncwarp();
+        float ebmax = 0.f;
+        for (int r = lane; r < rel; r += 32) ebmax = fmaxf(ebmax, eb[r]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ebmax = fmaxf(ebmax, __shfl_xor_sync(0xffffffffu, ebmax, o));
+        // two intervals meet when |v_r - v_q| <= b_r + b_q; compared in FP32 with a
+        // slack above the rounding of the values and of their difference, so a pair
+        // is never taken as apart when it is not.  The list is sorted, so each walk
+        // from r ends at the first entry beyond b_r + max b.
+        int open = 0;
+        for (int r0 = 0; r0 < rel; r0 += 32) {
+            const int r = r0 + lane;
+            bool o = false;
+            if (r < rel) {
+                o = (kk[r] & 0x40000000) != 0;
+                const float vr = fv[r], br = eb[r];
+                for (int q = min(r, n_t) - 1; q >= 0 && !o; q--) {   // higher values (a pair needs one of the first n_t)
+                    const float d = fv[q] - vr, sl = 2.4e-7f * (fv[q] + vr);
+                    if (d > br + ebmax + sl) break;
+                    const float sb = br + eb[q];
+                    o = sb > 0.f && fabsf(d) <= sb + sl;
+                }
+                for (int q = r + 1; r < n_t && q < rel && !o; q++) {   // lower values
+                    const float d = vr - fv[q], sl = 2.4e-7f * (fv[q] + vr);
+                    if (d > br + ebmax + sl) break;
+                    const float sb = br + eb[q];
+                    o = sb > 0.f && fabsf(d) <= sb + sl;
+                }
+                if (o) kk[r] |= 0x20000000;        // only lane r touches kk[r] here
+            }
+            open += __popc(__ballot_sync(0xffffffffu, o));
         }
         __syncwarp();
+        if (open == 0) break;
+        for (int r = 0; r < rel; r++) {
+            const int tag = kk[r];
+            if (!(tag & 0x20000000)) continue;
+            const int k = tag & 0x0fffffff;
+            if (tag & 0x10000000) {                // exact already: nothing to recompute
+                if (lane == 0) kk[r] = tag & ~0x20000000;
+                __syncwarp();
+                continue;
+            }
+            float bk = 0.f, bn = 0.f;
+            const double sk = tier == 1 ? window_acc(pts, m, (uint64_t)k, lane, bk) : window_fp64(pts, m, (uint64_t)k, lane);
+            int state = 1;                         // 1 a maximum, 0 not, 2 still uncertain
+            if (tag & 0x40000000) {                // S(k) > S(k - 1) and S(k) >= S(k + 1) at this accuracy
+                if (k > 0) {
+                    const double sl = tier == 1 ? window_acc(pts, m, (uint64_t)(k - 1), lane, bn)
+                                                : window_fp64(pts, m, (uint64_t)(k - 1), lane);
+                    if (sk - sl > (double)(bk + bn)) state = 1;
+                    else if (sl - sk >= (double)(bk + bn)) state = 0;
+                    else state = 2;
+                }
+                if (state != 0 && k < K - 1) {
+                    const double sr = tier == 1 ? window_acc(pts, m, (uint64_t)(k + 1), lane, bn)
+                                                : window_fp64(pts, m, (uint64_t)(k + 1), lane);
+                    if (sr - sk > (double)(bk + bn) || (tier == 2 && sr > sk)) state = 0;
+                    else if (!(sk - sr > (double)(bk + bn) || tier == 2)) state = 2;
+                }
+            }
+            if (lane == 0) {
+                val[r] = sk;
+                eb[r] = bk;
+                fv[r] = (float)sk;
+                kk[r] = state == 0 ? -1 : k | (state == 2 ? 0x40000000 : 0) | (tier == 2 ? 0x10000000 : 0);
+            }
+            __syncwarp();
+        }
     }
 
-    // the true maxima by value descending, ties to the lower k (insertion sort: only
-    // the recomputed entries can be out of place), the first n_t are the trials
+    // the first n_t of the decided order are the trials
     int32_t* out = a.trials + (int64_t)job * n_t;
+    for (int r = lane; r < n_t; r += 32) out[r] = r < rel ? (kk[r] & 0x0fffffff) : -1;
+    // a full candidate list leaves out points whose FP32 value is below its last
+    // entry: they cannot reach the trials when the n_t-th trial lies above it by
+    // more than both error bounds; otherwise (peaks of nearly equal height, such
+    // as the maxima 4 of a two-sample band) the band is scanned exactly
     int scan = 0;
-    if (lane == 0) {
-        int kept = 0;
-        for (int r = 0; r < rel; r++) {
-            if (kk[r] < 0) continue;
-            const double v = val[r];
-            const int k = kk[r] & 0x0fffffff;
-            const int tagged = k | (kk[r] & 0x10000000);   // keep the exact-value flag
-            int q = kept;
-            while (q > 0 && (val[q - 1] < v || (val[q - 1] == v && (kk[q - 1] & 0x0fffffff) > k))) {
-                val[q] = val[q - 1];
-                kk[q] = kk[q - 1];
-                q--;
-            }
-            val[q] = v;
-            kk[q] = tagged;
-            kept++;
-        }
-        for (int r = 0; r < n_t; r++) out[r] = r < kept ? (kk[r] & 0x0fffffff) : -1;
-        // a full candidate list leaves out points whose FP32 value is below its last
-        // entry: they cannot reach the trials when the n_t-th trial lies above it by
-        // more than both error bounds; otherwise (peaks of nearly equal height, such
-        // as the maxima 4 of a two-sample band) the band is scanned exactly
-        if (full) {
-            const double vt = kept >= n_t ? val[n_t - 1] : 0.0;
-            const double et = kept >= n_t && !(kk[n_t - 1] & 0x10000000) ? (double)win_err((float)vt, e) : 0.0;
-            scan = kept < n_t || vt - et <= (double)last32 + (double)win_err(last32, e);
-        }
-    }
+    if (full)
+        scan = rel < n_t || val[n_t - 1] - (double)eb[n_t - 1] <= (double)last32 + (double)win_err(last32, e);
     scan = __shfl_sync(0xffffffffu, scan, 0);
     if (!scan) return;
     if (lane == 0) atomicAdd(a.exact_scans, 1);
@@ -723,7 +825,7 @@ size_t window_smem_bytes(int max_band_points, int n_t) { return win_layout(max_b
 size_t refine_smem_bytes(int max_band_points, int n_t)
 {
     return (size_t)kRefineWarps * ((size_t)max_band_points * sizeof(ulonglong2) +
-                                   (size_t)win_candidates(n_t) * (sizeof(double) + sizeof(int32_t)));
+                                   (size_t)win_candidates(n_t) * (sizeof(double) + sizeof(int32_t) + 2 * sizeof(float)));
 }
 
 cudaError_t prepare_bands_kernels(int np2max, int max_band_points, int n_t)
