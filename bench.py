@@ -610,7 +610,7 @@ def main():
     if transforms is not None:
         line["transforms"] = transforms
     if getattr(g, "bands", False):
-        line["bands"] = {"kernels": "k_bands + k_window", "ms_per_step": float(info["last_bands_kernel_ms"]),
+        line["bands"] = {"kernels": "k_bands + k_window + k_window_refine", "ms_per_step": float(info["last_bands_kernel_ms"]),
                          "window_terms_per_s": info["window_terms_search"] / (info["last_bands_kernel_ms"] / 1e3),
                          "trials_per_curve": int(g.n_bands * g.trials_per_band)}
     if not args.no_cpu_baseline and world == 1:
