@@ -10,15 +10,20 @@
 //             on the uniform grid f_k = f_min + k df in FP32, one segment of
 //             the grid at a time in shared memory; the 2 n_t highest points
 //             that may be local maxima within the FP32 error bound (one-day
-//             frequencies left out) by a four-pass radix select on the value
-//             bits, merged into a running sorted candidate list, each
-//             candidate marked when its local-maximum test is certain.
+//             frequencies left out): a histogram of the candidates' value
+//             bits gives the bin of the segment's 2 n_t-th highest, the
+//             candidates at or above it are sorted and merged into a running
+//             sorted candidate list (an exact radix select on the value bits
+//             when that bin holds too many), each candidate marked when its
+//             local-maximum test is certain.
 //   k_window_refine  one warp per (curve, kept band): the exact choice.  Every
-//             candidate whose local-maximum test, or whose order against a
-//             neighbour in the list, lies within the FP32 error bound gets
-//             its window value(s) again in FP64 from the exact phases; the
-//             n_t highest true local maxima (value descending, ties to the
-//             lower k) are the trials, identical to an FP64 evaluation.
+//             candidate that can still reach the trials and whose
+//             local-maximum test, or whose order against another candidate,
+//             lies within the error bound gets its window value(s) again,
+//             first in an accurate FP32 form, then in FP64 from the exact
+//             phases; the n_t highest true local maxima (value descending,
+//             ties to the lower k) are the trials, identical to an FP64
+//             evaluation.
 //
 // Phases: exp(i 2 pi f_k t_i) with t_i - t0 (the window is invariant to a
 // common time shift) from the exact 64-bit fixed-point phases
@@ -200,6 +205,19 @@ __device__ __forceinline__ unsigned long long win_key(const float* S, int x, int
            (unsigned long long)(0x7fffffffu - (uint32_t)k);
 }
 
+__device__ __forceinline__ unsigned long long win_key_of(float v, bool sure, int k)
+{
+    return ((unsigned long long)orderable(v) << 32) | (sure ? 0x80000000ull : 0ull) |
+           (unsigned long long)(0x7fffffffu - (uint32_t)k);
+}
+
+// Histogram bin of a value S >= 0: the bits below the orderable form's top bit
+// (always set for S >= 0), as many as the bin count has.
+__device__ __forceinline__ int win_digit(float v, int shift, int bins)
+{
+    return (int)((orderable(v) >> shift) & (uint32_t)(bins - 1));
+}
+
 __device__ __forceinline__ bool win_cand(const uint32_t* mask, int j)
 {
     return (mask[j >> 5] >> (j & 31)) & 1u;
@@ -244,14 +262,21 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
     ulonglong2* pts = reinterpret_cast<ulonglong2*>(smem + Lo.pts);
     float4* rot = reinterpret_cast<float4*>(smem + Lo.rot);
     const int cap = pow2_at_least(win_candidates(a.n_t));
-    unsigned long long* sel = reinterpret_cast<unsigned long long*>(smem + Lo.lists);
-    unsigned long long* run0 = sel + cap;
-    unsigned long long* run1 = run0 + cap;
+    // lists: R0 R1 (the buffer of the fast path, the histogram before it; the
+    // fallback's selection and merge output), R2 (the running list)
+    unsigned long long* buf = reinterpret_cast<unsigned long long*>(smem + Lo.lists);
+    unsigned long long* sel = buf;
+    unsigned long long* nxt = buf + cap;
+    unsigned long long* run = buf + 2 * cap;
+    uint32_t* hist4 = reinterpret_cast<uint32_t*>(buf);   // 4 cap bins over R0 R1
+    const int hbins = 4 * cap;
+    int hshift = 31;                                       // digit = value bits 30 .. 31 - log2(hbins)
+    for (int b = hbins; b > 1; b >>= 1) hshift--;
     __shared__ uint32_t hist[256];
     __shared__ int s_wsum[kWinThreads / 32];
     __shared__ int s_total, s_nsel, s_m;
     __shared__ uint32_t s_prefix;
-    __shared__ int s_need, s_eq;
+    __shared__ int s_need, s_eq, s_d0, s_fast;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kWinThreads / 32;
@@ -293,9 +318,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
     const int m = min(s_m, a.max_band_points);
     const float e2 = win_term_err(m);   // per-term error scale of the band's window values
 
-    unsigned long long* run = run0;   // running list: the n_t highest so far, descending
-    unsigned long long* nxt = run1;
-    int rc = 0;
+    int rc = 0;                       // running list: the n_t highest so far, descending
     for (int lo = 0; lo < K; lo += kWinSeg) {
         const int hi = min(K, lo + kWinSeg);
         const int v0 = max(lo - 1, 0), v1 = min(hi + 1, K);   // S[k - v0] holds k in [v0, v1)
@@ -345,31 +368,44 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
                 if (jb < nv) S[jb] = m <= 1 ? (float)m : fmaf(rh, rh, ih * ih);
             }
         }
-        if (tid == 0) { s_total = 0; s_nsel = 0; }
+        if (tid == 0) { s_total = 0; s_nsel = 0; s_d0 = 0; s_fast = 1; }
+        for (int i = tid; i < hbins; i += kWinThreads) hist4[i] = 0u;
         __syncthreads();
 
         // 3. candidates of the segment: points that can be local maxima S[k] > S[k-1],
         //    S[k] >= S[k+1] (grid ends: one neighbour) within the error bound, one-day
         //    frequencies left out; once the running list is full, only keys above its
-        //    last entry can still enter it
+        //    last entry can still enter it.  Each value's bound is computed once (the
+        //    neighbours' come from the adjacent lanes), and a histogram of the
+        //    candidates' value bits is kept for the threshold of step 4.
         const unsigned long long floor_key = rc == n_t ? run[n_t - 1] : 0ull;
         const int len = hi - lo;
         const int words = (len + 31) >> 5;
         int local = 0;
-        for (int w = warp; w < words; w += NW) {
+#pragma unroll 2
+        for (int w = warp; w < words; w += NW) {   // warp-uniform: every lane takes the shuffles
             const int j = (w << 5) + lane;      // segment position, k = lo + j
             const int k = lo + j;
+            const int x = k - v0;
+            const bool in = j < len;
+            const float v = in ? S[x] : 0.f;
+            const float ev = in ? win_err(v, e2) : 0.f;
+            float vl = __shfl_up_sync(0xffffffffu, v, 1), el = __shfl_up_sync(0xffffffffu, ev, 1);
+            float vr = __shfl_down_sync(0xffffffffu, v, 1), er = __shfl_down_sync(0xffffffffu, ev, 1);
+            if (in && lane == 0 && k > 0) { vl = S[x - 1]; el = win_err(vl, e2); }
+            if (in && (lane == 31 || j + 1 >= len) && k < K - 1) { vr = S[x + 1]; er = win_err(vr, e2); }
             bool ok = false;
-            if (j < len) {
-                const int x = k - v0;
-                const float v = S[x];
+            if (in) {
                 // may be a local maximum in exact values: not decided against it by more
                 // than the two values' error bounds (exact bands: the exact test)
-                const float ev = win_err(v, e2);
-                const bool lok = k == 0 || (e2 > 0.f ? v >= S[x - 1] - ev - win_err(S[x - 1], e2) : v > S[x - 1]);
-                const bool rok = k == K - 1 || v >= S[x + 1] - ev - win_err(S[x + 1], e2);
-                ok = lok && rok && !(k >= a.ex_lo && k <= a.ex_hi) && win_key(S, x, k, K, e2) > floor_key;
+                const bool lok = k == 0 || (e2 > 0.f ? v >= vl - ev - el : v > vl);
+                const bool rok = k == K - 1 || v >= vr - ev - er;
+                if (lok && rok && !(k >= a.ex_lo && k <= a.ex_hi)) {
+                    const bool sure = (k == 0 || v - vl > ev + el) && (k == K - 1 || v - vr > ev + er);
+                    ok = win_key_of(v, sure, k) > floor_key;
+                }
             }
+            if (ok) atomicAdd(&hist4[win_digit(v, hshift, hbins)], 1u);
             const uint32_t bal = __ballot_sync(0xffffffffu, ok);
             if (lane == 0) {
                 mask[w] = bal;
@@ -380,6 +416,88 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
         __syncthreads();
         const int total = s_total;
 
+        // 4. fast path: the buffer (2 cap) takes the running list and the candidates
+        //    whose histogram bin is at or above the bin of the segment's n_t-th
+        //    largest (all of them when they fit); one sort keeps the n_t highest.
+        if (rc + total > 2 * cap && warp == 0) {
+            const int G = (hbins + 31) / 32;   // lane l owns bins hbins-1-lG down to hbins-(l+1)G
+            uint32_t sum = 0;
+            for (int y = 0; y < G; y++) {
+                const int d = hbins - 1 - lane * G - y;
+                if (d >= 0) sum += hist4[d];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t excl = incl - sum;
+            if (excl < (uint32_t)n_t && (uint32_t)n_t <= incl) {   // one lane: total > n_t here
+                uint32_t cum = excl;
+                for (int y = 0; y < G; y++) {
+                    const int d = hbins - 1 - lane * G - y;
+                    cum += hist4[d];
+                    if (cum >= (uint32_t)n_t) {
+                        s_d0 = d;
+                        s_fast = rc + (int)cum <= 2 * cap;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (s_fast) {
+            // the candidates in bins >= d0 into the buffer, in segment order: each warp
+            // counts its own, then writes at its offset (no atomics on the path)
+            const int d0 = s_d0;
+            int mine = 0;
+            for (int w = warp; w < words; w += NW) {
+                const uint32_t bits = mask[w];
+                bool take = false;
+                if ((bits >> lane) & 1u) take = win_digit(S[lo + (w << 5) + lane - v0], hshift, hbins) >= d0;
+                mine += __popc(__ballot_sync(0xffffffffu, take));
+            }
+            if (lane == 0) s_wsum[warp] = mine;
+            __syncthreads();
+            int off = 0, nsel = 0;
+            for (int w = 0; w < NW; w++) {
+                if (w < warp) off += s_wsum[w];
+                nsel += s_wsum[w];
+            }
+            for (int w = warp; w < words; w += NW) {
+                const uint32_t bits = mask[w];
+                const int j = (w << 5) + lane;
+                bool take = false;
+                if ((bits >> lane) & 1u) take = win_digit(S[lo + j - v0], hshift, hbins) >= d0;
+                const uint32_t tb = __ballot_sync(0xffffffffu, take);
+                if (take) buf[off + __popc(tb & ((1u << lane) - 1u))] = win_key(S, lo + j - v0, lo + j, K, e2);
+                off += __popc(tb);
+            }
+            // sort the new keys; merge their first n_t with the running list into R1
+            // (R1 is free, or holds sorted keys ranked below n_t)
+            const int np2 = pow2_at_least(nsel);
+            for (int i = nsel + tid; i < np2; i += kWinThreads) buf[i] = 0ull;
+            sort_desc(buf, np2, tid);
+            const int ns = min(nsel, n_t);
+            for (int i = tid; i < rc; i += kWinThreads) {
+                const int r = i + count_greater(buf, ns, run[i]);
+                if (r < n_t) nxt[r] = run[i];
+            }
+            for (int i = tid; i < ns; i += kWinThreads) {
+                const int r = i + count_greater(run, rc, buf[i]);
+                if (r < n_t) nxt[r] = buf[i];
+            }
+            rc = min(rc + ns, n_t);
+            __syncthreads();
+            for (int i = tid; i < rc; i += kWinThreads) run[i] = nxt[i];
+            __syncthreads();
+            continue;
+        }
+
+        // Fallback (the buffer would overflow: many candidates within one bin, such
+        // as the equal maxima of a two-sample band): the exact selection of the
+        // segment's n_t highest by a radix select on the value bits, then a merge.
         // 4. the segment's threshold: its n_t-th largest candidate value (radix select on the
         //    orderable bits, warp-aggregated histogram updates)
         uint32_t T = 0u;        // take keys > T, plus `need` keys == T (lowest k first)
@@ -496,9 +614,8 @@ __global__ void __launch_bounds__(kWinThreads) k_window(const WindowArgs a)
             if (r < n_t) nxt[r] = sel[i];
         }
         rc = min(rc + nsel, n_t);
-        unsigned long long* t = run;
-        run = nxt;
-        nxt = t;
+        __syncthreads();
+        for (int i = tid; i < rc; i += kWinThreads) run[i] = nxt[i];
         __syncthreads();
     }
 

@@ -188,3 +188,32 @@ def test_bands_full_size_sampled():
         peak = np.max(np.abs(ref[r][v]))
         assert np.max(np.abs(tr["trial_stat"][c][v] - ref[r][v])) <= TOL_DIRECT * peak
     assert np.all(best["best_idx"] >= 0)
+
+
+def test_bands_many_equal_height_maxima():
+    """Two-sample bands whose samples lie ~2000 d apart: each window is
+    2 + 2 cos(2 pi f dt), a local maximum every ~5 grid points, all of them
+    between 3.6 and 4.  A window segment of 8,190 points then holds ~1,600
+    candidates within one histogram bin, more than the selection buffer takes,
+    so the segment goes through the exact radix selection; the lists must
+    still equal the oracle's.  A ragged curve beside them keeps the common
+    path in the same launch."""
+    rng = np.random.default_rng(11)
+    n = 20
+    t = np.sort(rng.uniform(0.0, 4000.0, n))
+    t[10:] = np.maximum(t[10:], t[:10] + 1900.0 + 100.0 * rng.uniform(size=10))
+    t = np.sort(t)
+    rank = np.empty(n, np.int64)
+    rank[:10] = 2 * np.arange(10)              # band b holds samples b and b + 10 (time order)
+    rank[10:] = 2 * np.arange(10) + 1
+    y = 16.0 + 0.05 * rank + 1e-3 * rng.uniform(size=n)
+    e = 0.02 + 0.01 * rng.uniform(size=n)
+    r = synth.ragged_batch(1, seed=5, n_lo=300, n_hi=400)
+    tr_, yr, er = r.curve(0)
+    b = synth.Batch(np.concatenate([t, tr_]), np.concatenate([y, yr]).astype(np.float32),
+                    np.concatenate([e, er]).astype(np.float32), np.array([0, n, n + tr_.shape[0]], np.int64),
+                    np.zeros(2), np.zeros(2, bool), np.zeros(2, np.int8))
+    g = synth.Grid(0.00125, 1e-4, 29988, bands=True, n_bands=3, trials_per_band=150)
+    _, tr, info = run(b, g, sigma_t=0.3)
+    print("equal-height maxima: %d band lists chosen by a whole-grid FP64 scan" % info["bands_exact_scans"])
+    check_trials(b, g, tr["trial_idx"], [0, 1])
