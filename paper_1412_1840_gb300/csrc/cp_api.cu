@@ -118,6 +118,7 @@ struct cp_plan_s {
     int n_max = 0;                     // harmonics of the tensor form
     void* d_W16 = nullptr;             // pre-swizzled W' tiles (tensor form)
     float* d_coef = nullptr;           // [n_curves * n_max]
+    float* d_wrho = nullptr;           // tensor form: per sample, row sum of the 16-bit operand's rounding error
 
     // device buffers
     void* dblock = nullptr;              // one allocation for everything below
@@ -419,6 +420,8 @@ cp_status enqueue_stats(cp_plan_t p, cudaStream_t s)
     a.alpha = p->opt.alpha;
     a.np2max = p->np2max;
     a.status = reinterpret_cast<int*>(status_word(p));
+    a.wrho = p->tensor ? p->d_wrho : nullptr;
+    a.wrho_bf16 = p->opt.dtype == CP_DTYPE_BF16 ? 1 : 0;
     CP_CUDA(launch_stats(a, (int)p->n_curves, s));
     if (p->tensor) CP_CUDA(launch_harmonic_coef(p->d_cp, (int)p->n_curves, kCoefStride, p->d_coef, s));
     return CP_OK;
@@ -495,6 +498,7 @@ cp_status enqueue_wave_w(cp_plan_t p, int w, cudaStream_t s)
         b.order = p->d_order;
         b.wtile_start = p->d_wtile;
         b.yp = p->d_yp;
+        b.wrho = p->d_wrho;
         b.W16 = p->d_W16;
         b.slot_begin = wv.slot_begin;
         b.slot_end = wv.slot_end;
@@ -1084,6 +1088,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         {(void**)&p->d_W, (size_t)max_tiles32 * tile32_bytes},
         {(void**)&p->d_W16, (size_t)max_tiles16 * tile16_bytes},
         {(void**)&p->d_coef, p->tensor ? (size_t)nc * kCoefStride * sizeof(float) : 0},
+        {(void**)&p->d_wrho, p->tensor ? np * sizeof(float) : 0},
         {(void**)&p->d_coarse, hier ? (size_t)nc * p->kc * sizeof(float) : 0},
         {(void**)&p->d_peaks, hier ? (size_t)nc * g.top_k * sizeof(int32_t) : 0},
         {(void**)&p->d_npeaks, hier ? nc * sizeof(int32_t) : 0},

@@ -17,6 +17,8 @@
 //   nCKP = sqrt(N sigma_t) / IP * CKP = S sqrt(N) / (N^2 ip sqrt(2 pi) sqrt(sigma_t))
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "cp.h"
@@ -46,6 +48,8 @@ struct CurveParams {
     double t0;        // min t of the curve
     float st_floor;   // smallest sigma_t the curve's planned evaluation class covers
                       // (tensor form: its harmonic count's truncation target; else 0)
+    float dwsum;      // tensor form: sum over all (i, j) of the 16-bit operand's rounding
+                      // error of w_ij (the row sums per sample are in StatsArgs::wrho)
 };
 
 // sigma_t = 0.1 + 0.5 exp(-12 S^2), S the Bowley skewness of the magnitudes
@@ -117,6 +121,20 @@ __device__ __forceinline__ double grid_freq(double base, double k, double step)
     return __dadd_rn(base, __dmul_rn(k, step));
 }
 
+// Rounding error of the tensor form's 16-bit magnitude-kernel operand for one
+// entry w: FP16 round(w) - w, or for BF16 (hi + lo) - w with hi = bf16(w),
+// lo = bf16(w - hi) (the operand is stored as those two parts).  The tile
+// builder stores exactly these values; the statistics kernel sums the errors.
+__device__ __forceinline__ float w16_err(float w, bool bf)
+{
+    if (bf) {
+        const float hi = __bfloat162float(__float2bfloat16_rn(w));
+        const float lo = __bfloat162float(__float2bfloat16_rn(w - hi));
+        return (hi + lo) - w;
+    }
+    return __half2float(__float2half_rn(w)) - w;
+}
+
 struct PairArgs {
     const CurveParams* cp;       // [n_curves]
     const int32_t* order;        // sorted slot -> curve (N descending)
@@ -166,6 +184,8 @@ struct StatsArgs {
     float alpha;
     int np2max;
     int* status;
+    float* wrho;      // tensor form: per sample, sum_j of the 16-bit rounding error of w_ij (else null)
+    int wrho_bf16;    // that operand is BF16 hi + lo (else FP16)
 };
 
 struct BuildWArgs {
@@ -213,6 +233,7 @@ struct BuildW16Args {
     const int32_t* order;
     const int64_t* wtile_start;   // first W' tile of each slot (128 x 64 tiles)
     const float* yp;
+    const float* wrho;            // per sample: row sums of the operand's rounding error
     void* W16;
     int slot_begin, slot_end;
     int64_t tile_begin, tile_end;

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsArgs a)
     float* ypl = es + a.np2max;
     __shared__ double s_red[kStatsThreads / 32];
     __shared__ double s_t0;
-    __shared__ float s_yref, s_gamma;
+    __shared__ float s_yref, s_gamma, s_iph, s_ipl;
     __shared__ int s_bad;
 
     const int c = blockIdx.x;
@@ -188,9 +188,42 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsArgs a)
         P->ip = ip;
         P->ip_hi = iph;
         P->ip_lo = (float)(ip - (double)iph);
+        s_iph = iph;
+        s_ipl = P->ip_lo;
         P->norm = (float)(sqrt(nn) / (nn * nn * ip * sqrt(2.0 * CP_PI) * sqrt((double)P->sigma_t)));
         P->diag = (float)(nn * (1.0 - ip));
         if (s_bad) atomicOr(a.status, 1);
+    }
+
+    // 5b. tensor form: per sample i, the sum over j of the rounding error of the
+    //     16-bit operand w_ij = (g_ij - ip_hi) - ip_lo (the same FP32 values the
+    //     tile builder rounds), and its total.  With these the tensor epilogue
+    //     removes the error's coherent part: for a Z column x with mean xm the
+    //     operand error adds xm^2 sum(dW) + 2 xm drho^T (x - xm), which does not
+    //     average out where x is nearly constant over the samples (low f T, or
+    //     aliases of the sampling).  Full rows in a fixed order: deterministic.
+    if (a.wrho) {
+        __syncthreads();
+        const float iph = s_iph, ipl = s_ipl;
+        const bool bf = a.wrho_bf16 != 0;
+        double tot = 0.0;
+        for (int i = tid; i < n; i += kStatsThreads) {
+            const float yi = ypl[i];
+            float sum = 0.f;
+            for (int j = 0; j < n; j++) sum += w16_err((gauss_g(yi, ypl[j]) - iph) - ipl, bf);
+            a.wrho[off + i] = sum;
+            tot += (double)sum;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        __syncthreads();
+        if (lane == 0) s_red[warp] = tot;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kStatsThreads / 32; w++) t += s_red[w];
+            P->dwsum = (float)t;
+        }
     }
 
     // 6. fixed-point phase steps of t - t0 for each grid the search uses

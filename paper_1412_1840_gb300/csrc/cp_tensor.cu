@@ -78,6 +78,13 @@ constexpr int kTcTablePoints = 1024;   // per-unit phase table in shared memory 
 __device__ __forceinline__ int tc_tab(int j) { return j + (j >> 3); }
 constexpr int kTcTableSlots = kTcTablePoints + kTcTablePoints / 8;
 
+// Two pseudo-rows precede the samples in W' (rows 0 and 1 of its first
+// M-tile, whose block row spans every K chunk): row 0 holds the row sums of
+// the 16-bit rounding error of W, drho_j, row 1 ones.  Their products with a Z
+// column are drho^T z and 1^T z, from which the epilogue removes the coherent
+// part of the operand's rounding error (see k_stats).  Row / K index r is
+// sample r - kTcPseudo; the pseudo-rows' own Z rows are zero.
+constexpr int kTcPseudo = 2;
 __host__ __device__ inline int tc_mtiles(int n) { return (n + 127) / 128; }
 __host__ __device__ inline int tc_kchunks(int n) { return (n + 63) / 64; }
 __host__ __device__ inline int tc_tiles_of(int n)
@@ -124,7 +131,7 @@ __global__ void __launch_bounds__(256) k_build_w16(const BuildW16Args a)
     }
     const int c = a.order[lo];
     const CurveParams P = a.cp[c];
-    const int n = P.n, nkc = tc_kchunks(n);
+    const int n = P.n, nkc = tc_kchunks(n + kTcPseudo);
     int t = (int)(T - a.wtile_start[lo]);
     int I = 0;
     while (t >= nkc - 2 * I) { t -= nkc - 2 * I; ++I; }
@@ -132,8 +139,8 @@ __global__ void __launch_bounds__(256) k_build_w16(const BuildW16Args a)
     const float scale = (J >= 2 * I + 2) ? 2.0f : 1.0f;
     const int r = threadIdx.x >> 1;                 // tile row
     const int kb = (threadIdx.x & 1) * 32;          // first of 32 columns
-    const int i = I * 128 + r;
-    const float ypi = i < n ? a.yp[P.off + i] : 0.f;
+    const int i = I * 128 + r - kTcPseudo;          // sample of the row (-2, -1: pseudo-rows)
+    const float ypi = i >= 0 && i < n ? a.yp[P.off + i] : 0.f;
     const bool bf = a.bf16 != 0;
     // tile T: its tc_wparts(bf) parts (hi, then lo for BF16) of kTcA bytes each
     unsigned char* dst = reinterpret_cast<unsigned char*>(a.W16) + (T - a.tile_begin) * (int64_t)(tc_wparts(bf) * kTcA);
@@ -146,9 +153,13 @@ __global__ void __launch_bounds__(256) k_build_w16(const BuildW16Args a)
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const int k = kb + ch * 8 + e + h;
-                const int j = J * 64 + k;
+                const int j = J * 64 + k - kTcPseudo;
                 float w = 0.f;
-                if (i < n && j < n) w = ((gauss_g(ypi, a.yp[P.off + j]) - P.ip_hi) - P.ip_lo) * scale;
+                if (j >= 0 && j < n) {
+                    if (i >= 0 && i < n) w = ((gauss_g(ypi, a.yp[P.off + j]) - P.ip_hi) - P.ip_lo) * scale;
+                    else if (i == -kTcPseudo) w = a.wrho[P.off + j];
+                    else if (i == 1 - kTcPseudo) w = 1.0f;
+                }
                 v2[h] = w;
             }
             const uint16_t h0 = to16(v2[0], bf), h1 = to16(v2[1], bf);
@@ -265,8 +276,8 @@ __device__ __forceinline__ TcUnit tc_decode(const TensorArgs& a, int64_t u)
     const int slot = lo;
     U.c = a.order[slot];
     U.n = a.cp[U.c].n;
-    U.nmt = tc_mtiles(U.n);
-    U.nkc = tc_kchunks(U.n);
+    U.nmt = tc_mtiles(U.n + kTcPseudo);
+    U.nkc = tc_kchunks(U.n + kTcPseudo);
     U.wbase = a.wtile_start[slot] - a.wtile_base;
     const int64_t chunk = u - a.unit_start[slot];
     const int ft = 128 / a.n_max;
@@ -341,6 +352,8 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     __shared__ int s_abort;
     __shared__ float s_red[8][32];
     __shared__ float s_acc[32];                       // per-accumulator reduction: running sums
+    __shared__ __align__(16) float s_pse[kTcPseudo][kTcCols];   // the pseudo-rows' accumulator values of the unit
+    __shared__ float s_cc[kTcCols / 8];               // their correction, summed per 8 columns
 
     constexpr int FT = 128 / NMAX;                    // frequencies per unit
     constexpr int COLS = FT * 2 * NMAX;               // columns of the unit: 256, or 240 for 12 harmonics
@@ -504,8 +517,8 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                 bool live[2];
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    const int i = (2 * P + h) * 128 + row;
-                    live[h] = i < U.n;
+                    const int i = (2 * P + h) * 128 + row - kTcPseudo;   // sample of this row
+                    live[h] = (unsigned)i < (unsigned)U.n;
                     if (live[h]) {
                         pstep[h] = a.ph_step[off + i];
                         ph0[h] = a.ph_base[off + i] + tc_base_mult<LIST>(a, U) * pstep[h];
@@ -590,6 +603,22 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                             }
                         }
                     }
+                    // the pseudo-rows (first M-tile: lanes 0 and 1 of lane group 0) keep their
+                    // values for the unit's correction: one more read of this warp's columns
+                    if (has && P == 0 && h == 0 && lg == 0) {
+                        const uint32_t tb0 = taddr + (uint32_t)hcol;
+#pragma unroll 1
+                        for (int c0 = 0; c0 < FH * 2 * NMAX; c0 += 32) {
+                            float v[32];
+                            tmem_ld32(tb0 + c0, v);
+                            if (lane < kTcPseudo) {
+                                float4* dst = reinterpret_cast<float4*>(&s_pse[lane][hcol + c0]);
+#pragma unroll
+                                for (int q = 0; q < 8; q++)
+                                    dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                            }
+                        }
+                    }
                     // release this accumulator (always, so the phases of both buffers advance per pair)
                     tc_fence_before();
                     mbar_arrive(&bar_tempty[h]);
@@ -609,6 +638,32 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                 }
             }
             if (!ok) break;
+            // The unit's correction for the coherent part of the operand's rounding error.
+            // Per column, with the pseudo-rows' D0 = drho^T z and D1 = 1^T z (z = a_n x when
+            // the weights are folded into Z, else x) and xm = 1^T x / N, that error adds
+            // a_n (2 xm drho^T x - xm^2 sum dW).  Columns are spread over the epilogue
+            // threads and summed in groups of eight (2 n_max is a multiple of 8).
+            if (U.nmt <= 2) asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");   // stash of pair 0
+            {
+                const float inv_n = 1.0f / (float)U.n, dws = P_.dwsum;
+                for (int c0 = ew * 32; c0 < COLS; c0 += 32 * EW) {
+                    const int col = c0 + lane;
+                    float cc = 0.f;
+                    if (col < COLS) {
+                        const float an = a.coef[(int64_t)U.c * a.coef_stride + ((col % (2 * NMAX)) >> 1)];
+                        if (an > 0.f) {
+                            const float d0 = s_pse[0][col], d1 = s_pse[1][col];
+                            const float xm = FOLD ? __fdividef(d1 * inv_n, an) : d1 * inv_n;
+                            cc = an * xm * (2.f * (FOLD ? __fdividef(d0, an) : d0) - xm * dws);
+                        }
+                    }
+                    cc += __shfl_xor_sync(0xffffffffu, cc, 4);
+                    cc += __shfl_xor_sync(0xffffffffu, cc, 2);
+                    cc += __shfl_xor_sync(0xffffffffu, cc, 1);
+                    if ((lane & 7) == 0 && col < COLS) s_cc[col >> 3] = cc;
+                }
+            }
+            if constexpr (!UNIT_RED) asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
             if constexpr (UNIT_RED) {
                 // unit complete: sum over the rows (lanes, then the four lane groups), fixed order
                 const float x = warp_reduce_scatter<FHP>(accu, lane);
@@ -625,6 +680,10 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                 unsigned long long key = 0ull;
                 if (lane < U.count) {
                     if constexpr (!UNIT_RED) S = s_acc[lane];
+                    float corr = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 2 * NMAX / 8; q++) corr += s_cc[lane * (2 * NMAX / 8) + q];
+                    S -= corr;
                     const float v = S * P_.norm;
                     const long long kk = U.kfirst + lane;
                     if (a.stage == kStageFull) {
@@ -675,7 +734,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
             const TcUnit U = tc_decode(a, u);
             if (U.empty) continue;
             const int64_t off = a.cp[U.c].off;
-            const bool tab = U.n <= kTcTablePoints;
+            const bool tab = U.n + kTcPseudo <= kTcTablePoints;   // table slot = K row (sample + kTcPseudo)
             const uint64_t mf = tc_mult<LIST>(a, U, f);   // this producer's frequency multiplier
             const float* anp = a.coef + (int64_t)U.c * a.coef_stride + hr * NH;   // a_n of this harmonic range
             if (tab) {
@@ -685,7 +744,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                     const uint64_t stp = a.ph_step[off + j];
                     uint64_t ph0 = a.ph_base[off + j] + tc_base_mult<LIST>(a, U) * stp;
                     if (a.stage == kStageFine) ph0 += U.peak_mult * a.ph_coarse[off + j];
-                    sPh[tc_tab(j)] = make_ulonglong2(ph0, stp);
+                    sPh[tc_tab(j + kTcPseudo)] = make_ulonglong2(ph0, stp);
                 }
                 asm volatile("bar.sync 2, %0;" ::"n"(PROD) : "memory");
             }
@@ -693,17 +752,17 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                 for (int J = 4 * P; J < U.nkc; J++, q++) {
                     if (!active || (int)(q % (uint32_t)groups) != grp) continue;
                     const int s = q % STG;
-                    const int j0 = J * 64 + g * 8;
+                    const int j0 = J * 64 + g * 8;               // the octet's first K row (sample + kTcPseudo)
                     uint32_t pu[8];
 #pragma unroll
                     for (int p = 0; p < 8; p++) {
                         uint32_t v = 0u;
-                        if (j0 + p < U.n) {
+                        if ((unsigned)(j0 + p - kTcPseudo) < (unsigned)U.n) {
                             if (tab) {
                                 const ulonglong2 e = sPh[tc_tab(j0 + p)];
                                 v = (uint32_t)((e.x + mf * e.y) >> 32);
                             } else {
-                                v = tc_phase_u32<LIST>(a, U, off, j0 + p, mf);
+                                v = tc_phase_u32<LIST>(a, U, off, j0 + p - kTcPseudo, mf);
                             }
                         }
                         pu[p] = v;
@@ -720,7 +779,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                             for (int h = 0; h < 2; h++) {
                                 const int p = 2 * r + h;
                                 sv[h] = 0.f; cv[h] = 0.f; sb[h] = 0.f; cb[h] = 0.f; sa[h] = 0.f; ca[h] = 0.f;
-                                if (j0 + p < U.n) {
+                                if ((unsigned)(j0 + p - kTcPseudo) < (unsigned)U.n) {
                                     sincos2pi_turns_sfu(pu[p], sv[h], cv[h]);   // Z is rounded to 16 bits
                                     if (HS > 1 && hr > 0) {
                                         const uint32_t n0 = (uint32_t)(hr * NH + 1);
@@ -774,7 +833,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
 #pragma unroll
                         for (int p = 0; p < 8; p++) {
                             float sv = 0.f, cv = 0.f, sb = 0.f, cb = 0.f, sa = 0.f, ca = 0.f;
-                            if (j0 + p < U.n) {
+                            if ((unsigned)(j0 + p - kTcPseudo) < (unsigned)U.n) {
                                 sincos2pi_turns_sfu(pu[p], sv, cv);   // Z is rounded to 16 bits
                                 if (HS > 1 && hr > 0) {
                                     const uint32_t n0 = (uint32_t)(hr * NH + 1);
@@ -834,7 +893,7 @@ size_t tensor_smem_bytes(bool bf16)
 
 size_t tensor_tile_bytes(bool bf16) { return (size_t)tc_wparts(bf16) * kTcA; }
 
-int tensor_tiles_of(int n) { return tc_tiles_of(n); }
+int tensor_tiles_of(int n) { return tc_tiles_of(n + kTcPseudo); }
 
 template <int NMAX, bool BF>
 static cudaError_t set_tensor_smem()
