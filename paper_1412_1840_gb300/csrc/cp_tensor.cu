@@ -371,8 +371,8 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     // 16 harmonics, where the former raises register spills.
     constexpr bool UNIT_RED = NMAX != 16;
     // Epilogue angles by the SFU approximations (absolute error ~1e-6, far below the
-    // 16-bit rounding of Z); kept exact where the SFU form raised register spills.
-    constexpr bool EPI_SFU = NMAX == 4 || NMAX == 8 || NMAX == 16;
+    // 16-bit rounding of Z), for every class.
+    constexpr bool EPI_SFU = true;
     // a producer's harmonic range starts at n0 = hr NH + 1 with sigma_{n0-1} = sigma_{n0} = +
     static_assert(!FOLD || HS == 1 || NH % 4 == 0, "harmonic ranges must start on the sign pattern's period");
     static_assert(!FOLD || NH % 2 == 0, "the producers take the step's sign from the parity of nn");
