@@ -83,3 +83,34 @@ def test_random_batches_both_forms(seed):
     check(out, best, ref, 1e-5, "direct seed %d" % seed)
     out, best = periodogram(b, g, sigma_t=sigma_t, form=cp.CP_FORM_TENSOR, n_max=0)
     check(out, best, ref, 1e-3, "tensor seed %d" % seed)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_bands_trial_lists(seed):
+    """Bands method on random batches and grids (1-4 kept bands, 1-200 trials
+    per band, grids of 50-20,000 points): the trial lists are index work and
+    must equal the oracle's entry by entry wherever the oracle's band order is
+    decided (its derivative sums separated)."""
+    rng = np.random.default_rng(5000 + seed)
+    b, _, _ = random_case(5000 + seed)
+    n_bands = int(rng.integers(1, 5))
+    n_t = int(rng.integers(1, 201))
+    f_min = float(rng.uniform(0.0005, 1.0))
+    df = float(10.0 ** rng.uniform(-4.5, -2.5))
+    n_freq = int(rng.integers(50, 20001))
+    g = synth.Grid(f_min, df, n_freq, bands=True, n_bands=n_bands, trials_per_band=n_t)
+    with cp.Plan(b.times, b.mags, b.errs, b.offsets, cp.grid_from(g), sigma_t=0.3) as p:
+        p.best_period()
+        idx = p.trials()["trial_idx"].astype(np.int64)
+    ref = oracle.batch_bands_trials(b, g)
+    checked = 0
+    for c in range(b.n_curves):
+        t, m, _ = b.curve(c)
+        y = m.astype(np.float64)
+        D = np.sort(oracle.band_derivative_sums(t, y, oracle.bands_of(y)))[::-1]
+        if not all(D[q] - D[q + 1] > 1e-9 * max(D[0], 1e-300) or D[q] == D[q + 1] == 0.0
+                   for q in range(min(n_bands, 9))):
+            continue
+        np.testing.assert_array_equal(idx[c], ref[c], err_msg="seed %d curve %d" % (seed, c))
+        checked += 1
+    assert checked > 0 or b.n_curves == 0
