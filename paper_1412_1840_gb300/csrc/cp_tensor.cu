@@ -21,6 +21,12 @@
 // tiles (cos/sin of every harmonic by the Chebyshev recurrence) straight into
 // the swizzled shared-memory layout the MMA reads.  Every wait is bounded.
 //
+// The 16-bit rounding of W' leaves, per column, an error whose coherent part
+// (xm^2 sum dW + 2 xm drho^T (x - xm), xm the samples' mean of the column's x)
+// does not average out where x is nearly constant over the samples (f = 0,
+// short f T, aliases of the sampling); two pseudo-rows at the top of W' give
+// the products the epilogue needs to subtract it (see kTcPseudo).
+//
 // With folded weights both sides run the recurrence on x_n = sigma_n (cos n th,
 // sin n th) with the sign pattern sigma = +, +, -, -, ... (period 4 in n,
 // n = 0, 1, 2, ...).  Then x_{n+1} = K_n x_n + x_{n-1} with K_n = +2 cos th for
@@ -71,8 +77,8 @@ __host__ __device__ constexpr int tc_gstride(int nmax) { return (tc_items(nmax) 
 // (padded to 96 threads) produce three stages at once.
 __host__ __device__ constexpr int tc_producers(int nmax) { return nmax == 12 ? 288 : 256; }
 __host__ __device__ constexpr int tc_threads(int nmax) { return 64 + 32 * tc_ew(nmax) + tc_producers(nmax); }
-constexpr int kTcTablePoints = 1024;   // per-unit phase table in shared memory (producers)
-// Table slot of point j: one 16-byte pad after every 8 entries, so that the
+constexpr int kTcTablePoints = 1024;   // per-unit phase table in shared memory (producers), by K row
+// Table slot of K row j: one 16-byte pad after every 8 entries, so that the
 // eight j-octets a warp reads at once (128 bytes apart unpadded) fall on
 // different banks.
 __device__ __forceinline__ int tc_tab(int j) { return j + (j >> 3); }
