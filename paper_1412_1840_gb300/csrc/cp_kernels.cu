@@ -337,6 +337,11 @@ constexpr bool kPrefetchW = kItemRows == 4;   // next item's W in registers (the
 // Curves with sigma_t at or above this take the exponent in the cos form (see
 // pair_item); below it the sin form keeps the exponent's rounding relative.
 constexpr float kCosFormMinSigma = 0.3f;
+// The unit's trig table is built by one thread per (point, half of the
+// frequency pairs): each point's phase and step are loaded twice per unit
+// instead of once per frequency pair, and the threads' shares stay even
+// (one thread per point leaves a few threads with twice the work).
+constexpr int kTableGroups = 2;
 
 // One work item (4 kItemRows rows x 32 columns of a tile) at every frequency
 // pair of the unit.  The exponent of the periodic kernel (Eq. (periodickernel)),
@@ -461,39 +466,46 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
         f2* NS = reinterpret_cast<f2*>(SC + nfp * npad);
         const bool cosf = P.sigma_t >= kCosFormMinSigma;
         const float ts = cosf ? P.tscale * P.tscale * 0.70710678f : P.tscale;   // tscale^4 = beta
-        for (int it = tid; it < nfp * npad; it += kPairThreads) {
-            const int fp = it / npad, i = it - fp * npad;
-            ulonglong2 v = make_ulonglong2(0ull, 0ull);
-            f2 ns = 0ull;
+        // One thread per (point, group of frequency pairs): the point's phase and
+        // step are loaded once for the whole group, and the phase advances by two
+        // grid steps per pair (exact in the 2^-64 fixed point).
+        const int gsz = (nfp + kTableGroups - 1) / kTableGroups;
+        for (int it = tid; it < kTableGroups * npad; it += kPairThreads) {
+            const int gi = it / npad, i = it - gi * npad;
+            const int fp0 = gi * gsz, fp1 = min(nfp, fp0 + gsz);
             if (i < n) {
                 const uint64_t st = a.ph_step[off + i];
-                uint64_t ph = a.ph_base[off + i] + (uint64_t)(kfirst + 2 * fp) * st;
-                uint64_t ph1 = ph + st;
-                if (a.stage == kStageFine) {
-                    ph += peak_mult * a.ph_coarse[off + i];
-                    ph1 = ph + st;
-                } else if (a.stage == kStageList) {
-                    // grid indices of list positions kfirst + 2 fp (+1); a missing entry evaluates k = 0
-                    const long long q0 = kfirst + 2 * fp;
-                    const int k0 = q0 < a.n_trials ? max(tl[q0], 0) : 0;
-                    const int k1 = q0 + 1 < a.n_trials ? max(tl[q0 + 1], 0) : 0;
-                    ph = a.ph_base[off + i] + (uint64_t)k0 * st;
-                    ph1 = a.ph_base[off + i] + (uint64_t)k1 * st;
+                const uint64_t base = a.ph_base[off + i];
+                uint64_t ph = base + (uint64_t)(kfirst + 2 * fp0) * st;
+                if (a.stage == kStageFine) ph += peak_mult * a.ph_coarse[off + i];
+                for (int fp = fp0; fp < fp1; fp++, ph += 2 * st) {
+                    uint64_t p0 = ph, p1 = ph + st;
+                    if (a.stage == kStageList) {
+                        // grid indices of list positions kfirst + 2 fp (+1); a missing entry evaluates k = 0
+                        const long long q0 = kfirst + 2 * fp;
+                        const int k0 = q0 < a.n_trials ? max(tl[q0], 0) : 0;
+                        const int k1 = q0 + 1 < a.n_trials ? max(tl[q0 + 1], 0) : 0;
+                        p0 = base + (uint64_t)k0 * st;
+                        p1 = base + (uint64_t)k1 * st;
+                    }
+                    float s0, c0, s1, c1;
+                    if (cosf) {
+                        sincos2pi_turns((uint32_t)(p0 >> 32), s0, c0);
+                        sincos2pi_turns((uint32_t)(p1 >> 32), s1, c1);
+                    } else {
+                        sincospi_turns((uint32_t)(p0 >> 32), s0, c0);
+                        sincospi_turns((uint32_t)(p1 >> 32), s1, c1);
+                    }
+                    s0 *= ts; c0 *= ts; s1 *= ts; c1 *= ts;
+                    SC[fp * npad + i] = make_ulonglong2(pk(s0, s1), pk(c0, c1));
+                    if (!cosf) NS[fp * npad + i] = pk(-s0, -s1);   // the cos form reads SC only
                 }
-                float s0, c0, s1, c1;
-                if (cosf) {
-                    sincos2pi_turns((uint32_t)(ph >> 32), s0, c0);
-                    sincos2pi_turns((uint32_t)(ph1 >> 32), s1, c1);
-                } else {
-                    sincospi_turns((uint32_t)(ph >> 32), s0, c0);
-                    sincospi_turns((uint32_t)(ph1 >> 32), s1, c1);
+            } else {
+                for (int fp = fp0; fp < fp1; fp++) {
+                    SC[fp * npad + i] = make_ulonglong2(0ull, 0ull);
+                    if (!cosf) NS[fp * npad + i] = 0ull;
                 }
-                s0 *= ts; c0 *= ts; s1 *= ts; c1 *= ts;
-                v = make_ulonglong2(pk(s0, s1), pk(c0, c1));
-                ns = pk(-s0, -s1);
             }
-            SC[it] = v;
-            NS[it] = ns;
         }
         __syncthreads();
 
