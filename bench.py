@@ -82,7 +82,8 @@ def parse():
     ap.add_argument("--form", default="direct", choices=["direct", "tensor"])
     ap.add_argument("--n-max", type=int, default=0, help="tensor-form harmonics (0: per curve)")
     ap.add_argument("--no-tensor", action="store_true", help="skip the tensor-form measurement")
-    ap.add_argument("--dtype", default="fp16", choices=["fp16", "bf16"], help="tensor-form operand type")
+    ap.add_argument("--dtype", default="fp16", choices=["fp16", "bf16", "bf16split"],
+                    help="tensor-form operand type (bf16split: W' and Z both as hi + lo BF16 parts)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-transforms", action="store_true", help="skip timing preprocessing and whitening")
@@ -249,6 +250,7 @@ def main():
     import torch
     import paper_1412_1840_gb300 as cp
     from paper_1412_1840_gb300.shard import curve_ranges, gather_results, local_csr, max_over_ranks
+    DTYPES = {"fp16": cp.CP_DTYPE_FP16, "bf16": cp.CP_DTYPE_BF16, "bf16split": cp.CP_DTYPE_BF16_SPLIT}
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -290,8 +292,7 @@ def main():
     tuning = None
     if args.tuning != "none" and os.path.exists(args.tuning):
         tuning = cp.tuning_from(args.tuning)
-    tkw = dict(n_max=args.n_max, dtype=cp.CP_DTYPE_BF16 if args.dtype == "bf16" else cp.CP_DTYPE_FP16,
-               tuning=tuning)
+    tkw = dict(n_max=args.n_max, dtype=DTYPES[args.dtype], tuning=tuning)
     plan = cp.Plan(td, md, ed, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=form,
                    device=local, stream=stream.cuda_stream, **tkw)
     n = b.n_curves
@@ -365,8 +366,7 @@ def main():
     # ---- tensor-core form on the same resident batch ---------------------
     tensor = None
     if not args.no_tensor and args.form == "direct":
-        tkw2 = dict(n_max=args.n_max, dtype=cp.CP_DTYPE_BF16 if args.dtype == "bf16" else cp.CP_DTYPE_FP16,
-                    tuning=tuning)
+        tkw2 = dict(n_max=args.n_max, dtype=DTYPES[args.dtype], tuning=tuning)
         tplan = cp.Plan(td, md, ed, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=cp.CP_FORM_TENSOR,
                         device=local, stream=stream.cuda_stream, **tkw2)
         tidx = np.empty(n, np.int64); tbf = np.empty(n, np.float64); tbs = np.empty(n, np.float32)
@@ -426,36 +426,41 @@ def main():
             thplan.close()
             tensor["e2e"] = {"value": n_job * te_steps / te_s, "unit": "lightcurves/s",
                              "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": te_steps}
-        # the other 16-bit operand type on the same batch (same plan shape, a few timed steps)
-        other = cp.CP_DTYPE_FP16 if args.dtype == "bf16" else cp.CP_DTYPE_BF16
-        oplan = cp.Plan(td, md, ed, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=cp.CP_FORM_TENSOR,
-                        device=local, stream=stream.cuda_stream, n_max=args.n_max, dtype=other, tuning=tuning)
-        oplan.best_period_into(tidx, tbf, tbs, tper, tps)
-        o_steps = max(1, min(args.steps, 3))
-        barrier()
-        o_ms = []
-        for k in range(o_steps):
-            oe0, oe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            flush.fill_(7 + k)
-            oe0.record(stream)
+        # the other 16-bit operand types on the same batch (same plan shape, a few timed steps)
+        operands = {"fp16": "FP16",
+                    "bf16": "W' as hi + lo BF16 parts (two MMAs per K slice), Z one BF16 part",
+                    "bf16split": "W' and Z both as hi + lo BF16 parts (Z's lo part in the upper half of the MMA "
+                                 "columns: two MMAs per K slice over half the frequencies per unit)"}
+        tensor["other_dtypes"] = []
+        for oname in [d for d in ("fp16", "bf16", "bf16split") if d != args.dtype]:
+            oplan = cp.Plan(td, md, ed, b.offsets, grid, sigma_t_mode=cp.CP_SIGMA_T_RULE, form=cp.CP_FORM_TENSOR,
+                            device=local, stream=stream.cuda_stream, n_max=args.n_max, dtype=DTYPES[oname],
+                            tuning=tuning)
             oplan.best_period_into(tidx, tbf, tbs, tper, tps)
-            oe1.record(stream)
+            o_steps = max(1, min(args.steps, 3))
             barrier()
-            o_ms.append(oe0.elapsed_time(oe1))
-        oi = oplan.info()
-        o_s = max_over_ranks(sum(o_ms) / 1e3, device=dev)
-        oplan.close()
-        orel = np.abs(tbs.astype(np.float64) - bs) / np.maximum(np.abs(bs.astype(np.float64)), 1e-30)
-        otf = oi["tensor_flops_search"] / (oi["last_tensor_kernel_ms"] / 1e3) / 1e12
-        tensor["other_dtype"] = {"dtype": "fp16" if other == cp.CP_DTYPE_FP16 else "bf16",
-                                 "value": n_job * o_steps / o_s, "unit": "lightcurves/s",
-                                 "ms_per_step": o_s * 1e3 / o_steps, "steps": o_steps,
-                                 "best_idx_agreement_vs_direct": float(np.mean(tidx == idx)),
-                                 "best_stat_max_rel_diff_vs_direct": float(orel.max()),
-                                 "within_1e-3_of_direct": bool(orel.max() <= 1e-3),
-                                 "operands": "W' as hi + lo BF16 parts (two MMAs per K slice), Z one BF16 part"
-                                 if other == cp.CP_DTYPE_BF16 else "FP16",
-                                 "tensor_tflops_algorithmic": otf}
+            o_ms = []
+            for k in range(o_steps):
+                oe0, oe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.fill_(7 + k)
+                oe0.record(stream)
+                oplan.best_period_into(tidx, tbf, tbs, tper, tps)
+                oe1.record(stream)
+                barrier()
+                o_ms.append(oe0.elapsed_time(oe1))
+            oi = oplan.info()
+            o_s = max_over_ranks(sum(o_ms) / 1e3, device=dev)
+            oplan.close()
+            orel = np.abs(tbs.astype(np.float64) - bs) / np.maximum(np.abs(bs.astype(np.float64)), 1e-30)
+            otf = oi["tensor_flops_search"] / (oi["last_tensor_kernel_ms"] / 1e3) / 1e12
+            tensor["other_dtypes"].append({
+                "dtype": oname, "value": n_job * o_steps / o_s, "unit": "lightcurves/s",
+                "ms_per_step": o_s * 1e3 / o_steps, "steps": o_steps,
+                "class_curves": dict(zip(["direct", "n4", "n8", "n12", "n16", "n32"], oi["class_curves"])),
+                "best_idx_agreement_vs_direct": float(np.mean(tidx == idx)),
+                "best_stat_max_rel_diff_vs_direct": float(orel.max()),
+                "within_1e-3_of_direct": bool(orel.max() <= 1e-3),
+                "operands": operands[oname], "tensor_tflops_algorithmic": otf})
 
     # ---- coarse-then-fine search on the same batch (both forms) -------------
     hier = None

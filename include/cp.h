@@ -51,7 +51,16 @@ typedef struct cp_plan_s *cp_plan_t;
 /* Evaluation form. */
 enum { CP_FORM_DIRECT = 0, /* FP32 pair sum, FP64-exact fixed-point phases          */
        CP_FORM_TENSOR = 1  /* Fourier/Bessel series, FP16/BF16 tcgen05 GEMMs        */ };
-enum { CP_DTYPE_FP16 = 0, CP_DTYPE_BF16 = 1 };
+/* Operand type of the tensor form (FP32 accumulation in every case).
+ * FP16: 11 significand bits; meets 1e-3 of the peak with single operands.
+ * BF16: 8 bits; the magnitude-kernel operand W' is split into hi + lo BF16
+ *       parts (two MMAs per K slice), the harmonic operand Z stays single:
+ *       ~1e-3 to 1.5e-3 of the peak on harmonic-rich curves.
+ * BF16_SPLIT: BF16 with both W' and Z split into hi + lo parts (the lo part
+ *       of Z in the upper half of each unit's MMA columns, so a unit covers
+ *       half the frequencies): meets 1e-3 in BF16 at about half BF16's rate;
+ *       harmonic counts 4, 8, 16 and 32 (a curve that would take 12 takes 16). */
+enum { CP_DTYPE_FP16 = 0, CP_DTYPE_BF16 = 1, CP_DTYPE_BF16_SPLIT = 2 };
 /* How sigma_t is chosen per curve. */
 enum { CP_SIGMA_T_FIXED = 0,     /* options.sigma_t for every curve                    */
        CP_SIGMA_T_PER_CURVE = 1, /* options.sigma_t_per_curve[c] (host array)          */
@@ -163,7 +172,8 @@ typedef struct {
     float alpha;                     /* error-bar correction factor of Eq. (pSNR), >0   */
     int32_t form;                    /* CP_FORM_*                                       */
     int32_t dtype;                   /* CP_DTYPE_* (tensor form only)                   */
-    int32_t n_max;                   /* harmonics of the tensor form (4, 8, 12, 16, 32); */
+    int32_t n_max;                   /* harmonics of the tensor form (4, 8, 12, 16, 32; */
+                                     /* 12 not with CP_DTYPE_BF16_SPLIT);               */
                                      /* 0 = per curve: the smallest of 8, 12, 16, 32 whose */
                                      /* truncation tail is <= 1e-4 of the kernel peak   */
                                      /* for the curve's sigma_t (computed on the device */

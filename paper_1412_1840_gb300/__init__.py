@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libcp.so")
 
 CP_OK, CP_EINVAL, CP_ENOMEM, CP_ECUDA, CP_ETIMEOUT, CP_ESTATE, CP_EUNSUPPORTED = range(7)
 CP_FORM_DIRECT, CP_FORM_TENSOR = 0, 1
-CP_DTYPE_FP16, CP_DTYPE_BF16 = 0, 1
+CP_DTYPE_FP16, CP_DTYPE_BF16, CP_DTYPE_BF16_SPLIT = 0, 1, 2
 CP_SIGMA_T_FIXED, CP_SIGMA_T_PER_CURVE, CP_SIGMA_T_RULE = 0, 1, 2
 CP_MEM_HOST, CP_MEM_DEVICE = 0, 1
 CP_SEARCH_FULL, CP_SEARCH_COARSE_FINE, CP_SEARCH_BANDS = 0, 1, 2

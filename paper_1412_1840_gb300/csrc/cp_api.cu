@@ -236,6 +236,9 @@ const std::vector<double>& harmonic_thresholds()
     return thr;
 }
 
+// W' is stored as hi + lo BF16 parts for both BF16 operand types.
+static bool w_bf16(int dtype) { return dtype == CP_DTYPE_BF16 || dtype == CP_DTYPE_BF16_SPLIT; }
+
 int harmonics_for(float sigma_t)
 {
     const std::vector<double>& thr = harmonic_thresholds();
@@ -421,7 +424,7 @@ cp_status enqueue_stats(cp_plan_t p, cudaStream_t s)
     a.np2max = p->np2max;
     a.status = reinterpret_cast<int*>(status_word(p));
     a.wrho = p->tensor ? p->d_wrho : nullptr;
-    a.wrho_bf16 = p->opt.dtype == CP_DTYPE_BF16 ? 1 : 0;
+    a.wrho_bf16 = w_bf16(p->opt.dtype) ? 1 : 0;
     CP_CUDA(launch_stats(a, (int)p->n_curves, s));
     if (p->tensor) CP_CUDA(launch_harmonic_coef(p->d_cp, (int)p->n_curves, kCoefStride, p->d_coef, s));
     return CP_OK;
@@ -504,7 +507,7 @@ cp_status enqueue_wave_w(cp_plan_t p, int w, cudaStream_t s)
         b.slot_end = wv.slot_end;
         b.tile_begin = wv.tile_begin;
         b.tile_end = wv.tile_end;
-        b.bf16 = p->opt.dtype == CP_DTYPE_BF16 ? 1 : 0;
+        b.bf16 = w_bf16(p->opt.dtype) ? 1 : 0;
         CP_CUDA(launch_build_w16(b, s));
         return CP_OK;
     }
@@ -547,7 +550,8 @@ TensorArgs tensor_args(const PairArgs& d, cp_plan_t p)
     t.top_k = d.top_k;
     t.fine_half = d.fine_half;
     t.n_max = p->n_max;
-    t.bf16 = p->opt.dtype == CP_DTYPE_BF16 ? 1 : 0;
+    t.bf16 = w_bf16(p->opt.dtype) ? 1 : 0;
+    t.zsplit = p->opt.dtype == CP_DTYPE_BF16_SPLIT ? 1 : 0;
     t.f_min = d.f_min;
     t.f_max = d.f_max;
     t.step = d.step;
@@ -576,6 +580,7 @@ cp_status enqueue_pair(cp_plan_t p, int stage, int w, float* out, cudaStream_t s
     if (p->waves[w].cls != 0) {
         TensorArgs t = tensor_args(a, p);
         t.n_max = p->waves[w].cls;
+        t.ft = tensor_freqs_per_unit(t.n_max, t.zsplit != 0);
         CP_CUDA(launch_pair_tensor(t, p->n_sm, s));
     } else {
         CP_CUDA(launch_pair_direct(a, p->pair_grid, p->pair_smem, s));
@@ -793,11 +798,13 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     if (opt.form != CP_FORM_DIRECT && opt.form != CP_FORM_TENSOR)
         return fail(CP_EINVAL, "cp_plan: form must be CP_FORM_DIRECT or CP_FORM_TENSOR");
     if (opt.form == CP_FORM_TENSOR) {
-        if (opt.dtype != CP_DTYPE_FP16 && opt.dtype != CP_DTYPE_BF16)
-            return fail(CP_EINVAL, "cp_plan: dtype must be CP_DTYPE_FP16 or CP_DTYPE_BF16");
+        if (opt.dtype != CP_DTYPE_FP16 && opt.dtype != CP_DTYPE_BF16 && opt.dtype != CP_DTYPE_BF16_SPLIT)
+            return fail(CP_EINVAL, "cp_plan: dtype must be CP_DTYPE_FP16, CP_DTYPE_BF16 or CP_DTYPE_BF16_SPLIT");
         if (opt.n_max != 0 && opt.n_max != 4 && opt.n_max != 8 && opt.n_max != 12 && opt.n_max != 16 &&
             opt.n_max != 32)
             return fail(CP_EINVAL, "cp_plan: n_max must be 0 (per curve), 4, 8, 12, 16 or 32");
+        if (opt.dtype == CP_DTYPE_BF16_SPLIT && opt.n_max == 12)
+            return fail(CP_EINVAL, "cp_plan: n_max 12 is not available with CP_DTYPE_BF16_SPLIT (4, 8, 16 or 32)");
         p->tensor = true;
         p->n_max = opt.n_max;
         // test hook: shorter bounded waits, to exercise the timeout path
@@ -966,6 +973,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             if (s2 != CP_OK) return s2;
             for (int64_t c = 0; c < n_curves; c++) {
                 int cl = harmonics_for(st[c]);
+                if (cl == 12 && opt.dtype == CP_DTYPE_BF16_SPLIT) cl = 16;   // no 12-harmonic split-Z class
                 const int tb = tune_bucket(tune, (int)(offsets[c + 1] - offsets[c]));
                 const int bit = cl == 8 ? 1 : cl == 16 ? 2 : cl == 32 ? 4 : cl == 12 ? 8 : 0;
                 if (tb >= 0 && bit && !(tune.tensor_classes[tb] & bit)) cl = 0;   // tuned: direct form is faster here
@@ -993,7 +1001,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     for (int64_t s = 0; s < n_curves; s++) {
         const int c = p->order[s];
         const int n = (int)(offsets[c + 1] - offsets[c]);
-        const int f = p->cls[c] ? 128 / p->cls[c] : p->fc[c];
+        const int f = p->cls[c] ? tensor_freqs_per_unit(p->cls[c], opt.dtype == CP_DTYPE_BF16_SPLIT) : p->fc[c];
         const double pairs = 0.5 * (double)n * (double)(n - 1);
         p->unit_full[s + 1] = p->unit_full[s] + (g.n_freq + f - 1) / f;
         p->unit_list[s + 1] = p->unit_list[s] + (p->n_trials + f - 1) / f;
@@ -1029,7 +1037,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
     CP_CUDA(cudaMemGetInfo(&free_b, &total_b));
     size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 3);
     if (const char* env = std::getenv("CP_W_BUDGET_KB")) budget = (size_t)std::atoll(env) << 10;
-    const size_t tile16_bytes = tensor_tile_bytes(opt.dtype == CP_DTYPE_BF16), tile32_bytes = kTileFloats * sizeof(float);
+    const size_t tile16_bytes = tensor_tile_bytes(w_bf16(opt.dtype)), tile32_bytes = kTileFloats * sizeof(float);
     int64_t max_tiles32 = 0, max_tiles16 = 0;
     {
         auto close_wave = [&](int sb, int se) {
@@ -1436,7 +1444,7 @@ cp_status cp_get_plan_info(cp_plan_t p, cp_plan_info* info)
     double wd = 0, wt = 0;
     for (const Wave& w : p->waves)
         (w.cls ? wt : wd) += (double)(w.tile_end - w.tile_begin) *
-                             (w.cls ? (double)tensor_tile_bytes(p->opt.dtype == CP_DTYPE_BF16) : (double)kTileFloats * 4);
+                             (w.cls ? (double)tensor_tile_bytes(w_bf16(p->opt.dtype)) : (double)kTileFloats * 4);
     info->w_bytes_direct = wd;
     info->w_bytes_tensor = wt;
     info->replans = p->replans;

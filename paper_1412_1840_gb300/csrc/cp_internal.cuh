@@ -262,6 +262,8 @@ struct TensorArgs {
     int32_t fine_half;
     int32_t n_max;
     int32_t bf16;
+    int32_t zsplit;               // Z as hi + lo BF16 parts (BF16 only)
+    int32_t ft;                   // frequencies per unit: (zsplit ? 64 : 128) / n_max
     double f_min, f_max, step, coarse_df;
     float* out;
     int64_t out_ld;
@@ -314,6 +316,7 @@ cudaError_t launch_window(const WindowArgs& a, cudaStream_t s);
 size_t tensor_smem_bytes(bool bf16);
 size_t tensor_tile_bytes(bool bf16);   // bytes of one stored W' tile (BF16: hi and lo parts)
 int tensor_tiles_of(int n);
+int tensor_freqs_per_unit(int n_max, bool zsplit);
 cudaError_t prepare_tensor_kernel(int n_max);
 cudaError_t launch_build_w16(const BuildW16Args& a, cudaStream_t s);
 cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max, float* coef, cudaStream_t s);

@@ -50,7 +50,15 @@ constexpr int kTcB = 32768;            // 256 x 64 x 2 B
 // the tolerance of 1e-3 (Z's rounding stays below it).  With BF16 operands W'
 // is therefore stored as two BF16 tiles, hi = bf16(w) and lo = bf16(w - hi),
 // and every K slice issues two MMAs into the same accumulator: W' carries ~16
-// significand bits, Z stays single.  FP16 (11 bits) needs no split.
+// significand bits.  FP16 (11 bits) needs no split.
+// Split Z (ZS, BF16 only): Z's single BF16 rounding still leaves ~1.5e-3 on
+// the harmonic-rich curves, so Z too is stored as hi + lo parts, the lo part
+// in the upper half of the unit's 256 MMA columns: a unit holds half the
+// frequencies, column c + 128 carries bf16(z - hi) of column c, and the
+// epilogue reads D[c] + D[c + 128] = W' (Z_hi + Z_lo) less the lo x lo
+// product (the W' lo MMA covers the first 128 columns only): three of the
+// four hi/lo products.  Harmonic counts 4, 8, 16 and 32 (a half unit of
+// exactly 128 columns).
 __host__ __device__ constexpr int tc_wparts(bool bf) { return bf ? 2 : 1; }
 // Stages of the operand ring: W' tiles (all parts) of two M-tiles + one Z tile.
 __host__ __device__ constexpr int tc_stages(bool bf) { return bf ? 2 : 3; }
@@ -63,20 +71,27 @@ constexpr int kTcCols = 256;           // columns per unit
 // number of frequencies: 12 harmonics keep 4 warps).  With 18 warps a quarter-SM
 // holds up to 5 of them, which caps registers at 96 per thread: enough
 // below 32 harmonics.
-__host__ __device__ constexpr int tc_ew(int nmax) { return nmax <= 16 && (128 / nmax / 2) % 2 == 0 ? 8 : 4; }
+__host__ __device__ constexpr int tc_cols_h(bool zs) { return zs ? 128 : 256; }   // MMA columns of one Z part
+__host__ __device__ constexpr int tc_ft(int nmax, bool zs) { return tc_cols_h(zs) / 2 / nmax; }   // frequencies per unit
+__host__ __device__ constexpr int tc_ew(int nmax, bool zs) { return nmax <= 16 && (tc_ft(nmax, zs) / 2) % 2 == 0 ? 8 : 4; }
 // Producer items split a frequency's harmonics into this many ranges for 32
 // harmonics (4 frequencies per unit): 64 items per stage instead of 32, so
 // three stages are produced by 192 threads instead of 96.
-__host__ __device__ constexpr int tc_hsplit(int nmax) { return nmax == 32 ? 2 : 1; }
+// With split Z a unit has half the frequencies, so the harmonic ranges are
+// halved too (8 and 16 harmonics: 2 ranges, 32: 4) to keep the items per stage.
+__host__ __device__ constexpr int tc_hsplit(int nmax, bool zs)
+{
+    return zs ? (nmax == 4 ? 1 : nmax == 32 ? 4 : 2) : (nmax == 32 ? 2 : 1);
+}
 // Items of one Z stage: (j-octet, frequency, harmonic range).  A stage group
 // takes a whole number of warps: a warp split between two groups would run
 // both groups' work one after the other.
-__host__ __device__ constexpr int tc_items(int nmax) { return 8 * (128 / nmax) * tc_hsplit(nmax); }
-__host__ __device__ constexpr int tc_gstride(int nmax) { return (tc_items(nmax) + 31) / 32 * 32; }
+__host__ __device__ constexpr int tc_items(int nmax, bool zs) { return 8 * tc_ft(nmax, zs) * tc_hsplit(nmax, zs); }
+__host__ __device__ constexpr int tc_gstride(int nmax, bool zs) { return (tc_items(nmax, zs) + 31) / 32 * 32; }
 // Producer threads: 8 warps; 9 for 12 harmonics, so that three 80-item groups
 // (padded to 96 threads) produce three stages at once.
 __host__ __device__ constexpr int tc_producers(int nmax) { return nmax == 12 ? 288 : 256; }
-__host__ __device__ constexpr int tc_threads(int nmax) { return 64 + 32 * tc_ew(nmax) + tc_producers(nmax); }
+__host__ __device__ constexpr int tc_threads(int nmax, bool zs) { return 64 + 32 * tc_ew(nmax, zs) + tc_producers(nmax); }
 constexpr int kTcTablePoints = 1024;   // per-unit phase table in shared memory (producers), by K row
 // Table slot of K row j: one 16-byte pad after every 8 entries, so that the
 // eight j-octets a warp reads at once (128 bytes apart unpadded) fall on
@@ -121,6 +136,13 @@ __device__ __forceinline__ uint32_t pack16x2(float lo, float hi)
     else
         asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
+}
+
+// The BF16 rounding residuals of a packed pair: (lo - bf16(lo), hi - bf16(hi))
+// (exact in FP32), rounded to BF16 and packed the same way.
+__device__ __forceinline__ uint32_t bf16x2_residual(float lo, float hi, uint32_t packed)
+{
+    return pack16x2<true>(lo - __uint_as_float(packed << 16), hi - __uint_as_float(packed & 0xffff0000u));
 }
 
 // ===========================================================================
@@ -286,7 +308,7 @@ __device__ __forceinline__ TcUnit tc_decode(const TensorArgs& a, int64_t u)
     U.nkc = tc_kchunks(U.n + kTcPseudo);
     U.wbase = a.wtile_start[slot] - a.wtile_base;
     const int64_t chunk = u - a.unit_start[slot];
-    const int ft = 128 / a.n_max;
+    const int ft = a.ft;
     U.peak = 0;
     U.peak_mult = 0;
     U.empty = false;
@@ -341,8 +363,9 @@ __device__ __forceinline__ uint32_t tc_phase_u32(const TensorArgs& a, const TcUn
 // 2P+1 share every Z stage of their common K range (two TMEM accumulators).
 // LIST: the list stage (explicit grid indices per curve); a separate
 // instantiation so that the uniform stages keep their rotation shortcut.
-template <int NMAX, bool BF, bool LIST>
-__global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const TensorArgs a)
+// ZS: Z split into hi + lo BF16 parts (see tc_cols_h).
+template <int NMAX, bool BF, bool LIST, bool ZS>
+__global__ void __launch_bounds__(tc_threads(NMAX, ZS), 1) k_pair_tensor(const TensorArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -361,16 +384,19 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
     __shared__ __align__(16) float s_pse[kTcPseudo][kTcCols];   // the pseudo-rows' accumulator values of the unit
     __shared__ float s_cc[kTcCols / 8];               // their correction, summed per 8 columns
 
-    constexpr int FT = 128 / NMAX;                    // frequencies per unit
-    constexpr int COLS = FT * 2 * NMAX;               // columns of the unit: 256, or 240 for 12 harmonics
-    constexpr int EW = tc_ew(NMAX);                   // epilogue warps
+    constexpr int FT = tc_ft(NMAX, ZS);               // frequencies per unit
+    constexpr int CH = FT * 2 * NMAX;                 // columns of one Z part: 256 (240 for 12 harmonics), 128 split
+    constexpr int COLS = ZS ? 2 * CH : CH;            // MMA columns of the unit
+    constexpr int LW = ZS ? 16 : 32;                  // accumulator columns per TMEM load
+    static_assert(!ZS || (BF && CH == 128), "split Z: BF16 operands and 4, 8, 16 or 32 harmonics");
+    constexpr int EW = tc_ew(NMAX, ZS);               // epilogue warps
     constexpr int FH = FT / (EW / 4);                 // frequencies per epilogue warp
     constexpr int FHP = FH <= 2 ? 2 : FH <= 4 ? 4 : FH <= 8 ? 8 : FH <= 16 ? 16 : 32;   // padded to a power of 2
-    constexpr int HS = tc_hsplit(NMAX);               // harmonic ranges per producer item
+    constexpr int HS = tc_hsplit(NMAX, ZS);           // harmonic ranges per producer item
     constexpr int NH = NMAX / HS;                     // harmonics per producer item
-    constexpr int items = tc_items(NMAX);             // (j-octet, frequency, harmonic range) per stage
+    constexpr int items = tc_items(NMAX, ZS);         // (j-octet, frequency, harmonic range) per stage
     constexpr int PROD = tc_producers(NMAX);
-    constexpr int GS = tc_gstride(NMAX);              // threads per stage group
+    constexpr int GS = tc_gstride(NMAX, ZS);          // threads per stage group
     constexpr bool FOLD = NMAX <= 16;                 // a_n folded into Z (see the file header)
     // Row sums reduced across the warp once per unit (per-thread partial sums over
     // the M-tiles) or once per accumulator; the latter measured faster only for
@@ -448,6 +474,9 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_f16(128, COLS, BF);
+            // W' lo against Z hi only: with split Z the lo x lo product (2^-18 of the
+            // term) is left out, an N = 128 MMA over the first half of the columns
+            constexpr uint32_t idesc_lo = idesc_f16(128, ZS ? CH : COLS, BF);
             uint32_t q = 0, m = 0;
             bool ok = true;
             for (int64_t u = a.unit_begin + blockIdx.x / a.ctas_per_unit; ok && u < a.unit_end; u += gridDim.x) {
@@ -474,11 +503,11 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                         for (int kk = 0; kk < 4; kk++) {
                             const uint64_t bd = sw128_desc(b0 + kk * 32);
                             umma_f16(taddr, sw128_desc(a0 + kk * 32), bd, idesc, (J > 2 * I0 || kk > 0) ? 1u : 0u);
-                            if (WP == 2) umma_f16(taddr, sw128_desc(a0 + kTcA + kk * 32), bd, idesc, 1u);
+                            if (WP == 2) umma_f16(taddr, sw128_desc(a0 + kTcA + kk * 32), bd, idesc_lo, 1u);
                             if (use1) {
                                 umma_f16(taddr + kTcCols, sw128_desc(a1 + kk * 32), bd, idesc,
                                          (J > 2 * I1 || kk > 0) ? 1u : 0u);
-                                if (WP == 2) umma_f16(taddr + kTcCols, sw128_desc(a1 + kTcA + kk * 32), bd, idesc, 1u);
+                                if (WP == 2) umma_f16(taddr + kTcCols, sw128_desc(a1 + kTcA + kk * 32), bd, idesc_lo, 1u);
                             }
                         }
                         umma_commit(&bar_empty[s]);
@@ -551,7 +580,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                     }
                     if (has) {
                         const uint32_t tbase = taddr + ((uint32_t)(lg * 32) << 16) + (uint32_t)(h * kTcCols) + hcol;
-                        float v[32];
+                        float v[LW];
                         // the angle of odd frequencies is the even one's rotated by one frequency step
                         float sr = 0.f, cr = 1.f, s1 = 0.f, c1 = 0.f;
                         if (live_h) epi_sincos<EPI_SFU>((uint32_t)(pstep_h >> 32), sr, cr);
@@ -574,8 +603,11 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
 #pragma unroll
                                 for (int n = 1; n <= NMAX; n++) {
                                     const int col = fi * 2 * NMAX + 2 * (n - 1);   // relative to hcol
-                                    if ((col & 31) == 0) tmem_ld32(tbase + col, v);
-                                    acc2 = fma2(pk(v[col & 31], v[(col & 31) + 1]), xc, acc2);
+                                    if (col % LW == 0) {
+                                        if constexpr (ZS) tmem_ld16_sum(tbase + col, tbase + CH + col, v);
+                                        else tmem_ld32(tbase + col, v);
+                                    }
+                                    acc2 = fma2(pk(v[col % LW], v[col % LW + 1]), xc, acc2);
                                     if (n < NMAX) {
                                         const f2 xn = fma2((n & 1) ? km : kp, xc, xp);
                                         xp = xc;
@@ -595,8 +627,11 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
 #pragma unroll
                                 for (int n = 1; n <= NMAX; n++) {
                                     const int col = fi * 2 * NMAX + 2 * (n - 1);   // relative to hcol
-                                    if ((col & 31) == 0) tmem_ld32(tbase + col, v);
-                                    acc = fmaf(an[n - 1], fmaf(v[col & 31], cp1, v[(col & 31) + 1] * sp1), acc);
+                                    if (col % LW == 0) {
+                                        if constexpr (ZS) tmem_ld16_sum(tbase + col, tbase + CH + col, v);
+                                        else tmem_ld32(tbase + col, v);
+                                    }
+                                    acc = fmaf(an[n - 1], fmaf(v[col % LW], cp1, v[col % LW + 1] * sp1), acc);
                                     const float cn = fmaf(2.f * c1, cp1, -cp2), sn = fmaf(2.f * c1, sp1, -sp2);
                                     cp2 = cp1; sp2 = sp1;
                                     cp1 = cn; sp1 = sn;
@@ -614,13 +649,14 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                     if (has && P == 0 && h == 0 && lg == 0) {
                         const uint32_t tb0 = taddr + (uint32_t)hcol;
 #pragma unroll 1
-                        for (int c0 = 0; c0 < FH * 2 * NMAX; c0 += 32) {
-                            float v[32];
-                            tmem_ld32(tb0 + c0, v);
+                        for (int c0 = 0; c0 < FH * 2 * NMAX; c0 += LW) {
+                            float v[LW];
+                            if constexpr (ZS) tmem_ld16_sum(tb0 + c0, tb0 + CH + c0, v);
+                            else tmem_ld32(tb0 + c0, v);
                             if (lane < kTcPseudo) {
                                 float4* dst = reinterpret_cast<float4*>(&s_pse[lane][hcol + c0]);
 #pragma unroll
-                                for (int q = 0; q < 8; q++)
+                                for (int q = 0; q < LW / 4; q++)
                                     dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                             }
                         }
@@ -652,10 +688,10 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
             if (U.nmt <= 2) asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");   // stash of pair 0
             {
                 const float inv_n = 1.0f / (float)U.n, dws = P_.dwsum;
-                for (int c0 = ew * 32; c0 < COLS; c0 += 32 * EW) {
+                for (int c0 = ew * 32; c0 < CH; c0 += 32 * EW) {
                     const int col = c0 + lane;
                     float cc = 0.f;
-                    if (col < COLS) {
+                    if (col < CH) {
                         const float an = a.coef[(int64_t)U.c * a.coef_stride + ((col % (2 * NMAX)) >> 1)];
                         if (an > 0.f) {
                             const float d0 = s_pse[0][col], d1 = s_pse[1][col];
@@ -666,7 +702,7 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                     cc += __shfl_xor_sync(0xffffffffu, cc, 4);
                     cc += __shfl_xor_sync(0xffffffffu, cc, 2);
                     cc += __shfl_xor_sync(0xffffffffu, cc, 1);
-                    if ((lane & 7) == 0 && col < COLS) s_cc[col >> 3] = cc;
+                    if ((lane & 7) == 0 && col < CH) s_cc[col >> 3] = cc;
                 }
             }
             if constexpr (!UNIT_RED) asm volatile("bar.sync 1, %0;" ::"n"(32 * EW) : "memory");
@@ -810,18 +846,26 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
                             const int n = hr * NH + 1 + nn;
                             const float an = __ldg(anp + nn);
                             const f2 a2 = pk(an, an);
-                            uint32_t pc[4], ps[4];
+                            uint32_t pc[4], ps[4], pcl[4], psl[4];
 #pragma unroll
                             for (int r = 0; r < 4; r++) {
                                 float lo, hi;
                                 upk(mul2(a2, cc[r]), lo, hi);
                                 pc[r] = pack16x2<BF>(lo, hi);
+                                if constexpr (ZS) pcl[r] = bf16x2_residual(lo, hi, pc[r]);
                                 upk(mul2(a2, ss[r]), lo, hi);
                                 ps[r] = pack16x2<BF>(lo, hi);
+                                if constexpr (ZS) psl[r] = bf16x2_residual(lo, hi, ps[r]);
                             }
                             const int col = f * 2 * NMAX + 2 * (n - 1);
                             *reinterpret_cast<uint4*>(Bs + sw128_offset(col, g * 8)) = make_uint4(pc[0], pc[1], pc[2], pc[3]);
                             *reinterpret_cast<uint4*>(Bs + sw128_offset(col + 1, g * 8)) = make_uint4(ps[0], ps[1], ps[2], ps[3]);
+                            if constexpr (ZS) {
+                                *reinterpret_cast<uint4*>(Bs + sw128_offset(CH + col, g * 8)) =
+                                    make_uint4(pcl[0], pcl[1], pcl[2], pcl[3]);
+                                *reinterpret_cast<uint4*>(Bs + sw128_offset(CH + col + 1, g * 8)) =
+                                    make_uint4(psl[0], psl[1], psl[2], psl[3]);
+                            }
                             if (nn + 1 < NH) {
 #pragma unroll
                                 for (int r = 0; r < 4; r++) {
@@ -858,15 +902,25 @@ __global__ void __launch_bounds__(tc_threads(NMAX), 1) k_pair_tensor(const Tenso
 #pragma unroll
                         for (int nn = 0; nn < NH; nn++) {
                             const int n = hr * NH + 1 + nn;
-                            uint32_t pc[4], ps[4];
+                            uint32_t pc[4], ps[4], pcl[4], psl[4];
 #pragma unroll
                             for (int p = 0; p < 8; p += 2) {
                                 pc[p >> 1] = pack16x2<BF>(cc[p], cc[p + 1]);
                                 ps[p >> 1] = pack16x2<BF>(ss[p], ss[p + 1]);
+                                if constexpr (ZS) {
+                                    pcl[p >> 1] = bf16x2_residual(cc[p], cc[p + 1], pc[p >> 1]);
+                                    psl[p >> 1] = bf16x2_residual(ss[p], ss[p + 1], ps[p >> 1]);
+                                }
                             }
                             const int col = f * 2 * NMAX + 2 * (n - 1);
                             *reinterpret_cast<uint4*>(Bs + sw128_offset(col, g * 8)) = make_uint4(pc[0], pc[1], pc[2], pc[3]);
                             *reinterpret_cast<uint4*>(Bs + sw128_offset(col + 1, g * 8)) = make_uint4(ps[0], ps[1], ps[2], ps[3]);
+                            if constexpr (ZS) {
+                                *reinterpret_cast<uint4*>(Bs + sw128_offset(CH + col, g * 8)) =
+                                    make_uint4(pcl[0], pcl[1], pcl[2], pcl[3]);
+                                *reinterpret_cast<uint4*>(Bs + sw128_offset(CH + col + 1, g * 8)) =
+                                    make_uint4(psl[0], psl[1], psl[2], psl[3]);
+                            }
 #pragma unroll
                             for (int p = 0; p < 8; p++) {
                                 const float cn = fmaf(2.f * c1[p], cc[p], -cm[p]);
@@ -901,26 +955,47 @@ size_t tensor_tile_bytes(bool bf16) { return (size_t)tc_wparts(bf16) * kTcA; }
 
 int tensor_tiles_of(int n) { return tc_tiles_of(n + kTcPseudo); }
 
-template <int NMAX, bool BF>
+template <int NMAX, bool BF, bool ZS>
 static cudaError_t set_tensor_smem()
 {
-    cudaError_t e = raise_dyn_smem((const void*)k_pair_tensor<NMAX, BF, false>, tensor_smem_bytes(BF));
+    cudaError_t e = raise_dyn_smem((const void*)k_pair_tensor<NMAX, BF, false, ZS>, tensor_smem_bytes(BF));
     if (e != cudaSuccess) return e;
-    return raise_dyn_smem((const void*)k_pair_tensor<NMAX, BF, true>, tensor_smem_bytes(BF));
+    return raise_dyn_smem((const void*)k_pair_tensor<NMAX, BF, true, ZS>, tensor_smem_bytes(BF));
 }
 
 cudaError_t prepare_tensor_kernel(int n_max)
 {
     cudaError_t e = cudaErrorInvalidValue;
     switch (n_max) {
-    case 4: e = set_tensor_smem<4, false>(); if (e == cudaSuccess) e = set_tensor_smem<4, true>(); break;
-    case 8: e = set_tensor_smem<8, false>(); if (e == cudaSuccess) e = set_tensor_smem<8, true>(); break;
-    case 12: e = set_tensor_smem<12, false>(); if (e == cudaSuccess) e = set_tensor_smem<12, true>(); break;
-    case 16: e = set_tensor_smem<16, false>(); if (e == cudaSuccess) e = set_tensor_smem<16, true>(); break;
-    case 32: e = set_tensor_smem<32, false>(); if (e == cudaSuccess) e = set_tensor_smem<32, true>(); break;
+    case 4:
+        e = set_tensor_smem<4, false, false>();
+        if (e == cudaSuccess) e = set_tensor_smem<4, true, false>();
+        if (e == cudaSuccess) e = set_tensor_smem<4, true, true>();
+        break;
+    case 8:
+        e = set_tensor_smem<8, false, false>();
+        if (e == cudaSuccess) e = set_tensor_smem<8, true, false>();
+        if (e == cudaSuccess) e = set_tensor_smem<8, true, true>();
+        break;
+    case 12:
+        e = set_tensor_smem<12, false, false>();
+        if (e == cudaSuccess) e = set_tensor_smem<12, true, false>();
+        break;
+    case 16:
+        e = set_tensor_smem<16, false, false>();
+        if (e == cudaSuccess) e = set_tensor_smem<16, true, false>();
+        if (e == cudaSuccess) e = set_tensor_smem<16, true, true>();
+        break;
+    case 32:
+        e = set_tensor_smem<32, false, false>();
+        if (e == cudaSuccess) e = set_tensor_smem<32, true, false>();
+        if (e == cudaSuccess) e = set_tensor_smem<32, true, true>();
+        break;
     }
     return e;
 }
+
+int tensor_freqs_per_unit(int n_max, bool zsplit) { return zsplit ? tc_ft(n_max, true) : tc_ft(n_max, false); }
 
 cudaError_t launch_build_w16(const BuildW16Args& a, cudaStream_t s)
 {
@@ -938,27 +1013,35 @@ cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max,
 
 cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s)
 {
-    const bool bf = a.bf16 != 0, list = a.stage == kStageList;
+    const bool bf = a.bf16 != 0, list = a.stage == kStageList, zs = a.zsplit != 0;
     const size_t b = tensor_smem_bytes(bf);
-#define CP_TC_LAUNCH(NM)                                                                        \
+    if (zs && (!bf || a.n_max == 12)) return cudaErrorInvalidValue;
+#define CP_TC_GO(NM, BFV, LV, ZV) k_pair_tensor<NM, BFV, LV, ZV><<<grid, tc_threads(NM, ZV), b, s>>>(a)
+#define CP_TC_LAUNCH(NM, ZOK)                                                                   \
     case NM:                                                                                    \
-        if (list) {                                                                             \
-            if (bf) k_pair_tensor<NM, true, true><<<grid, tc_threads(NM), b, s>>>(a);               \
-            else k_pair_tensor<NM, false, true><<<grid, tc_threads(NM), b, s>>>(a);                 \
+        if (zs) {                                                                               \
+            if constexpr (ZOK) {                                                                \
+                if (list) CP_TC_GO(NM, true, true, ZOK);                                        \
+                else CP_TC_GO(NM, true, false, ZOK);                                            \
+            }                                                                                   \
+        } else if (list) {                                                                      \
+            if (bf) CP_TC_GO(NM, true, true, false);                                            \
+            else CP_TC_GO(NM, false, true, false);                                              \
         } else {                                                                                \
-            if (bf) k_pair_tensor<NM, true, false><<<grid, tc_threads(NM), b, s>>>(a);              \
-            else k_pair_tensor<NM, false, false><<<grid, tc_threads(NM), b, s>>>(a);                \
+            if (bf) CP_TC_GO(NM, true, false, false);                                           \
+            else CP_TC_GO(NM, false, false, false);                                             \
         }                                                                                       \
         break;
     switch (a.n_max) {
-        CP_TC_LAUNCH(4)
-        CP_TC_LAUNCH(8)
-        CP_TC_LAUNCH(12)
-        CP_TC_LAUNCH(16)
-        CP_TC_LAUNCH(32)
+        CP_TC_LAUNCH(4, true)
+        CP_TC_LAUNCH(8, true)
+        CP_TC_LAUNCH(12, false)
+        CP_TC_LAUNCH(16, true)
+        CP_TC_LAUNCH(32, true)
     default: return cudaErrorInvalidValue;
     }
 #undef CP_TC_LAUNCH
+#undef CP_TC_GO
     return cudaGetLastError();
 }
 

@@ -142,11 +142,11 @@ def test_bands_edge_batch():
             assert not oracle.is_one_day(g.f_min + k * g.df)
 
 
-@pytest.mark.parametrize("n_max", [0, 16])
-def test_bands_tensor_form(small, n_max):
+@pytest.mark.parametrize("n_max,dtype", [(0, cp.CP_DTYPE_FP16), (16, cp.CP_DTYPE_FP16), (0, cp.CP_DTYPE_BF16_SPLIT)])
+def test_bands_tensor_form(small, n_max, dtype):
     b, g = small
     best_d, tr_d, _ = run(b, g, sigma_t=0.35)
-    best_t, tr_t, _ = run(b, g, sigma_t=0.35, form=cp.CP_FORM_TENSOR, n_max=n_max)
+    best_t, tr_t, _ = run(b, g, sigma_t=0.35, form=cp.CP_FORM_TENSOR, n_max=n_max, dtype=dtype)
     np.testing.assert_array_equal(tr_t["trial_idx"], tr_d["trial_idx"])   # same bands kernels
     valid = tr_d["trial_idx"] >= 0
     freqs = g.f_min + np.maximum(tr_d["trial_idx"], 0).astype(np.float64) * g.df

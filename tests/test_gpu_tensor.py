@@ -7,6 +7,7 @@ index is accepted at the same tolerance (c16 reading).  BF16 operands: the
 magnitude-kernel operand is split into two BF16 parts (hi + lo), so its
 rounding no longer counts; the Z operand's single BF16 rounding (8
 significand bits) leaves a floor near 1e-3, held here to BF16_TOL = 2e-3.
+BF16 with Z split as well (CP_DTYPE_BF16_SPLIT) is held to TOL.
 """
 import os
 
@@ -96,21 +97,50 @@ def test_tensor_bf16_parity_ragged(ragged, n_max):
     accept_best(best, ref, rows, BF16_TOL)
 
 
-def test_tensor_bf16_edge_batch_and_hierarchical():
+@pytest.mark.parametrize("n_max", [4, 8, 16, 32])
+def test_tensor_bf16_split_parity_ragged(ragged, n_max):
+    """BF16 with both operands split into hi + lo parts: the Z part's rounding
+    no longer counts either, and the form meets the tensor bar of 1e-3."""
+    b, g, ref = ragged
+    out, best, _ = run(b, g, sigma_t=0.45, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_BF16_SPLIT, n_max=n_max)
+    rows = range(b.n_curves)
+    err = peak_err(out, ref, rows)
+    print("\nBF16 split, %d harmonics: per-curve peak-relative error" % n_max, " ".join("%.2e" % x for x in err))
+    if n_max == 4:
+        # 4 harmonics truncate the series at sigma_t = 0.45 (both operand types alike):
+        # the split BF16 result must equal FP16's at the same count within 1e-3 of the peak
+        out16, _, _ = run(b, g, sigma_t=0.45, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_FP16, n_max=4)
+        d = peak_err(out, out16, rows)
+        assert np.all(err > 2e-3) and np.all(d <= TOL), d
+        return
+    assert np.all(err <= TOL), err
+    accept_best(best, ref, rows, TOL)
+
+
+def test_tensor_bf16_split_rejects_12_harmonics():
+    b = synth.ragged_batch(2, seed=21)
+    g = synth.Grid(0.002, 1e-4, 64)
+    with pytest.raises(cp.CpError) as e:
+        run(b, g, sigma_t=0.45, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_BF16_SPLIT, n_max=12)
+    assert e.value.status == cp.CP_EINVAL
+
+
+@pytest.mark.parametrize("dtype,tol", [(cp.CP_DTYPE_BF16, BF16_TOL), (cp.CP_DTYPE_BF16_SPLIT, TOL)])
+def test_tensor_bf16_edge_batch_and_hierarchical(dtype, tol):
     b = synth.edge_batch()
     g = synth.Grid(0.005, 0.005, 600)
-    out, best, _ = run(b, g, sigma_t=0.3, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_BF16, n_max=16)
+    out, best, _ = run(b, g, sigma_t=0.3, form=cp.CP_FORM_TENSOR, dtype=dtype, n_max=16)
     ref = oracle.batch_nckp(b, np.full(b.n_curves, float(np.float32(0.3))), g.freqs())
     rows = [c for c in range(b.n_curves) if c != 3]
     assert np.all(out[3] == 0.0)
     err = peak_err(out, ref, rows)
-    assert np.all(err <= BF16_TOL), err
-    accept_best(best, ref, rows, BF16_TOL)
+    assert np.all(err <= tol), err
+    accept_best(best, ref, rows, tol)
     b = synth.ragged_batch(6, seed=24, n_lo=100, n_hi=260, span=1200.0)
     g = synth.Grid(0.01, 1e-4, 19901, hierarchical=True, coarse_df=4e-3, top_k=10, fine_df=1e-4,
                    fine_halfwidth=4e-3)
     with cp.Plan(b.times, b.mags, b.errs, b.offsets, cp.grid_from(g), sigma_t=0.35, form=cp.CP_FORM_TENSOR,
-                 dtype=cp.CP_DTYPE_BF16, n_max=16) as p:
+                 dtype=dtype, n_max=16) as p:
         hb = p.best_period()
     st = float(np.float32(0.35))
     ref = oracle.batch_best(b, g, sigma_t=st)
@@ -118,7 +148,7 @@ def test_tensor_bf16_edge_batch_and_hierarchical():
         t, m, e = b.curve(c)
         v = oracle.nckp(t, m.astype(np.float64), oracle.median(e.astype(np.float64)), st, [hb["best_freq"][c]])[0]
         vstar = ref["best_stat"][c]
-        assert v >= vstar - BF16_TOL * abs(vstar) and abs(hb["best_stat"][c] - v) <= BF16_TOL * abs(vstar)
+        assert v >= vstar - tol * abs(vstar) and abs(hb["best_stat"][c] - v) <= tol * abs(vstar)
 
 
 def test_tensor_edge_batch():
@@ -201,6 +231,19 @@ def test_tensor_auto_harmonics_per_curve():
     err = peak_err(out, ref, range(b.n_curves))
     assert np.all(err <= TOL), err
     accept_best(best, ref, range(b.n_curves), TOL)
+    # split BF16: the 12-harmonic curve takes 16; every curve meets the same bar
+    with cp.Plan(b.times, b.mags, b.errs, b.offsets, cp.grid_from(g), sigma_t_per_curve=st,
+                 form=cp.CP_FORM_TENSOR, n_max=0, dtype=cp.CP_DTYPE_BF16_SPLIT) as p:
+        out = torch.empty((b.n_curves, g.n_freq), dtype=torch.float32, device="cuda")
+        p.periodogram(out)
+        p.sync()
+        best = p.best_period()
+        info = p.info()
+    assert info["class_curves"] == [2, 0, 2, 0, 3, 3]
+    err = peak_err(out.cpu().numpy(), ref, range(b.n_curves))
+    print("\nBF16 split, per-curve harmonics: per-curve peak-relative error", " ".join("%.2e" % x for x in err))
+    assert np.all(err <= TOL), err
+    accept_best(best, ref, range(b.n_curves), TOL)
 
 
 def test_tuning_table_moves_a_class_to_the_direct_form():
@@ -238,8 +281,10 @@ def test_error_matrix_on_benchmark_curves():
     ref = oracle.batch_nckp(sub, st.astype(np.float64), gs.freqs())
     rows = range(sub.n_curves)
     table = {}
-    for dtype, dname in ((cp.CP_DTYPE_FP16, "fp16"), (cp.CP_DTYPE_BF16, "bf16")):
+    for dtype, dname in ((cp.CP_DTYPE_FP16, "fp16"), (cp.CP_DTYPE_BF16, "bf16"), (cp.CP_DTYPE_BF16_SPLIT, "bf16 split")):
         for nm in (0, 8, 12, 16, 32):
+            if dtype == cp.CP_DTYPE_BF16_SPLIT and nm == 12:
+                continue
             out, _, _ = run(sub, gs, sigma_t_per_curve=st, form=cp.CP_FORM_TENSOR, dtype=dtype, n_max=nm)
             table[(dname, nm)] = float(peak_err(out, ref, rows).max())
     out, _, _ = run(sub, gs, sigma_t_per_curve=st)
@@ -251,9 +296,10 @@ def test_error_matrix_on_benchmark_curves():
     assert table[("fp16", 0)] <= TOL
     assert table[("fp32 direct", "-")] <= 1e-5
     assert table[("bf16", 0)] <= BF16_TOL
+    assert table[("bf16 split", 0)] <= TOL
 
 
-@pytest.mark.parametrize("dtype", [cp.CP_DTYPE_FP16, cp.CP_DTYPE_BF16])
+@pytest.mark.parametrize("dtype", [cp.CP_DTYPE_FP16, cp.CP_DTYPE_BF16, cp.CP_DTYPE_BF16_SPLIT])
 def test_full_size_tensor_form_sampled(dtype):
     """The 4096-curve, 49,981-frequency benchmark batch in the benchmark's
     tensor-form launch configuration (device inputs, sigma_t rule, per-curve
@@ -287,7 +333,7 @@ def test_full_size_tensor_form_sampled(dtype):
         ref = oracle.nckp(t, m.astype(np.float64), oracle.median(e.astype(np.float64)),
                           float(stats["sigma_t"][c]), f[ks])
         peak = max(abs(ref).max(), abs(rows[r]).max())
-        assert np.max(np.abs(rows[r][ks] - ref)) <= (TOL if dtype == cp.CP_DTYPE_FP16 else BF16_TOL) * peak, c
+        assert np.max(np.abs(rows[r][ks] - ref)) <= (BF16_TOL if dtype == cp.CP_DTYPE_BF16 else TOL) * peak, c
 
 
 def test_rule_mode_plan_follows_changed_magnitudes():
