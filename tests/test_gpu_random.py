@@ -4,7 +4,8 @@ sigma_t, through both forms of the pair sum, against the FP64 oracle.
 
 The bar is the one of the other parity tests: per curve, peak-relative nCKP
 error <= 1e-5 (direct FP32 form) and <= 1e-3 (tensor form, FP16 operands,
-harmonics per curve), and the c16 acceptance of the best index.
+harmonics per curve; BF16 with both operands split on every third case), and
+the c16 acceptance of the best index.
 """
 import numpy as np
 import pytest
@@ -83,6 +84,10 @@ def test_random_batches_both_forms(seed):
     check(out, best, ref, 1e-5, "direct seed %d" % seed)
     out, best = periodogram(b, g, sigma_t=sigma_t, form=cp.CP_FORM_TENSOR, n_max=0)
     check(out, best, ref, 1e-3, "tensor seed %d" % seed)
+    if seed % 3 == 0:   # BF16 with both operands split, on every third case
+        out, best = periodogram(b, g, sigma_t=sigma_t, form=cp.CP_FORM_TENSOR, n_max=0,
+                                dtype=cp.CP_DTYPE_BF16_SPLIT)
+        check(out, best, ref, 1e-3, "tensor bf16 split seed %d" % seed)
 
 
 @pytest.mark.parametrize("seed", range(12))
