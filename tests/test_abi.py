@@ -120,6 +120,27 @@ def test_argument_validation_precedes_device_use():
     assert _plan_status([0, 5], tuning=bad_mask) == cp.CP_EINVAL
 
 
+def test_binding_constants_match_header():
+    """Every CP_* enumerator of include/cp.h has the same value in the binding."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "cp.h")).read(), flags=re.S)
+    found = 0
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, val in re.findall(r"\b(CP_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            if hasattr(cp, name):
+                assert getattr(cp, name) == int(val), name
+                found += 1
+    assert found >= 10 and cp.CP_DTYPE_BF16_SPLIT == 2
+
+
+def test_tensor_operand_type_is_validated_before_device_use():
+    tensor = dict(form=cp.CP_FORM_TENSOR)
+    assert _plan_status([0, 5], dtype=3, **tensor) == cp.CP_EINVAL
+    assert _plan_status([0, 5], dtype=-1, **tensor) == cp.CP_EINVAL
+    # split Z has no 12-harmonic class
+    assert _plan_status([0, 5], dtype=cp.CP_DTYPE_BF16_SPLIT, n_max=12, **tensor) == cp.CP_EINVAL
+    assert _plan_status([0, 5], dtype=cp.CP_DTYPE_BF16, n_max=20, **tensor) == cp.CP_EINVAL
+
+
 def test_exclusion_windows_are_validated_before_device_use():
     """Section 6.1 windows: at most CP_MAX_EXCLUDE, finite lo <= hi; the
     no-allocation entry point refuses them (it has no plan to hold them)."""
