@@ -184,7 +184,7 @@ def cpu_baseline(b, g, target_s=15.0, max_curves=8):
     import oracle
     oracle.build()
     freqs = g.freqs()
-    cores = os.cpu_count() or 1
+    cores = oracle.max_threads()        # the threads its OpenMP loops actually run on
     nc = min(max_curves, b.n_curves)
     sub = b.subset(range(nc))
     k_sample = 256
@@ -224,6 +224,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    # rank 0 runs alone: give the oracle every host core (torchrun sets OMP_NUM_THREADS=1
+    # per rank; the variable is read when the oracle library is loaded, below)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
     b, g, name = make_workload(args, 0)
     per_step = []
     for _ in range(args.warmup + args.steps):

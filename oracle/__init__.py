@@ -68,6 +68,7 @@ def lib():
     if _lib is None:
         build()
         L = ctypes.CDLL(_LIB)
+        L.orc_max_threads.restype = ctypes.c_int; L.orc_max_threads.argtypes = []
         L.orc_gauss.restype = D; L.orc_gauss.argtypes = [D, D]
         L.orc_periodic_kernel.restype = D; L.orc_periodic_kernel.argtypes = [D, D, D]
         L.orc_information_potential.restype = D; L.orc_information_potential.argtypes = [PD, I64, D]
@@ -368,6 +369,11 @@ def batch_best(batch, grid, sigma_t_mode=0, sigma_t=0.3, sigma_t_per_curve=None,
     out["best_idx"] = out["best_idx"].astype(np.int64)
     out["is_periodic"] = out["is_periodic"].astype(bool)
     return out
+
+
+def max_threads() -> int:
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(lib().orc_max_threads())
 
 
 def batch_nckp(batch, sigma_t, freqs) -> np.ndarray:

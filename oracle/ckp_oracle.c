@@ -56,9 +56,13 @@
  *     folded positions k - w/2 .. k - w/2 + w - 1.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Threads the OpenMP loops of this file run on (reported beside timed runs). */
+int orc_max_threads(void) { return omp_get_max_threads(); }
 
 #define ORC_PI 3.14159265358979323846
 
