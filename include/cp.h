@@ -59,7 +59,8 @@ enum { CP_FORM_DIRECT = 0, /* FP32 pair sum, FP64-exact fixed-point phases      
  * BF16_SPLIT: BF16 with both W' and Z split into hi + lo parts (the lo part
  *       of Z in the upper half of each unit's MMA columns, so a unit covers
  *       half the frequencies): meets 1e-3 in BF16 at about half BF16's rate;
- *       harmonic counts 4, 8, 16 and 32 (a curve that would take 12 takes 16). */
+ *       harmonic counts 4, 8, 16 and 32 (a curve that would take 12 takes 16,
+ *       one that would take 48 runs in the direct form). */
 enum { CP_DTYPE_FP16 = 0, CP_DTYPE_BF16 = 1, CP_DTYPE_BF16_SPLIT = 2 };
 /* How sigma_t is chosen per curve. */
 enum { CP_SIGMA_T_FIXED = 0,     /* options.sigma_t for every curve                    */
@@ -150,9 +151,9 @@ typedef struct {
  *   direct_fc[b]       frequencies per work unit of the direct form (2, 4, 8
  *                      or 16; lowered to the largest that fits the kernel's
  *                      shared trig table for the curve's N);
- *   tensor_classes[b]  with n_max = 0, bit 0, 1, 2, 3 set lets the harmonic
- *                      class 8, 16, 32, 12 run in the tensor form; a curve whose
- *                      class bit is clear runs in the direct form.
+ *   tensor_classes[b]  with n_max = 0, bit 0, 1, 2, 3, 4 set lets the harmonic
+ *                      class 8, 16, 32, 12, 48 run in the tensor form; a curve
+ *                      whose class bit is clear runs in the direct form.
  * Curves above the last bucket, and plans without tuning, use the built-in
  * choices (16 frequencies per unit where they fit; every class in the tensor
  * form).  Results never depend on the tuning beyond the form's own rounding.
@@ -172,13 +173,15 @@ typedef struct {
     float alpha;                     /* error-bar correction factor of Eq. (pSNR), >0   */
     int32_t form;                    /* CP_FORM_*                                       */
     int32_t dtype;                   /* CP_DTYPE_* (tensor form only)                   */
-    int32_t n_max;                   /* harmonics of the tensor form (4, 8, 12, 16, 32; */
-                                     /* 12 not with CP_DTYPE_BF16_SPLIT);               */
-                                     /* 0 = per curve: the smallest of 8, 12, 16, 32 whose */
-                                     /* truncation tail is <= 1e-4 of the kernel peak   */
-                                     /* for the curve's sigma_t (computed on the device */
-                                     /* at plan time); curves that need more run in the */
-                                     /* direct form.  Each call checks, on the device,  */
+    int32_t n_max;                   /* harmonics of the tensor form (4, 8, 12, 16, 32, */
+                                     /* 48; 12 and 48 not with CP_DTYPE_BF16_SPLIT);    */
+                                     /* 0 = per curve: the smallest of 8, 12, 16, 32, 48 */
+                                     /* whose truncation tail is <= 1e-4 of the kernel  */
+                                     /* peak for the curve's sigma_t (computed on the   */
+                                     /* device at plan time; 48 covers sigma_t >= 0.1,  */
+                                     /* the rule's smallest value); curves that need    */
+                                     /* more (or 48 with split Z) run in the direct     */
+                                     /* form.  Each call checks, on the device,         */
                                      /* that every curve's current sigma_t is still     */
                                      /* covered by its count; if one is not (the        */
                                      /* magnitudes changed, e.g. by cp_whiten), the     */
@@ -325,8 +328,8 @@ typedef struct {
     float last_step_ms;           /* device time of the whole last cp_best_period       */
     int32_t n_sm;                 /* SMs of the plan's device                           */
     int32_t max_n;                /* largest N in the batch                             */
-    int64_t class_curves[6];      /* curves per evaluation class: direct form, then the */
-                                  /* tensor form with 4, 8, 12, 16, 32 harmonics        */
+    int64_t class_curves[7];      /* curves per evaluation class: direct form, then the */
+                                  /* tensor form with 4, 8, 12, 16, 32, 48 harmonics    */
     float last_tensor_kernel_ms;  /* device time of the tensor-form launches, last call */
     float last_direct_kernel_ms;  /* device time of the direct-form launches, last call */
     double tensor_flops_search;   /* tensor-form GEMM flops of one cp_best_period:      */

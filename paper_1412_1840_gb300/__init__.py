@@ -70,7 +70,8 @@ def tuning_from(table) -> cp_tuning:
     for i, bk in enumerate(buckets):
         t.bucket_max_n[i] = int(bk["max_n"])
         t.direct_fc[i] = int(bk["direct_fc"])
-        t.tensor_classes[i] = sum(1 << k for k, cl in enumerate(("8", "16", "32", "12")) if bk["tensor"].get(cl, True))
+        t.tensor_classes[i] = sum(1 << k for k, cl in enumerate(("8", "16", "32", "12", "48"))
+                                  if bk["tensor"].get(cl, True))
     return t
 
 
@@ -86,7 +87,7 @@ class cp_plan_info(ctypes.Structure):
     _fields_ = [("n_curves", ctypes.c_int64), ("n_points", ctypes.c_int64), ("pair_freq_full", ctypes.c_double),
                 ("pair_freq_search", ctypes.c_double), ("launches_per_search", ctypes.c_int64),
                 ("last_pair_kernel_ms", ctypes.c_float), ("last_step_ms", ctypes.c_float),
-                ("n_sm", ctypes.c_int32), ("max_n", ctypes.c_int32), ("class_curves", ctypes.c_int64 * 6),
+                ("n_sm", ctypes.c_int32), ("max_n", ctypes.c_int32), ("class_curves", ctypes.c_int64 * 7),
                 ("last_tensor_kernel_ms", ctypes.c_float), ("last_direct_kernel_ms", ctypes.c_float),
                 ("tensor_flops_search", ctypes.c_double), ("direct_pair_freq_search", ctypes.c_double),
                 ("last_bands_kernel_ms", ctypes.c_float), ("reserved0", ctypes.c_float),

@@ -108,7 +108,7 @@ struct cp_plan_s {
     std::vector<int32_t> order;          // slot -> curve
     std::vector<int32_t> fc;             // per curve
     std::vector<int32_t> cls;            // per curve: 0 direct, else tensor harmonics
-    int64_t class_count[6] = {0, 0, 0, 0, 0, 0};   // curves per class {direct, 4, 8, 12, 16, 32}
+    int64_t class_count[7] = {0, 0, 0, 0, 0, 0, 0};   // curves per class {direct, 4, 8, 12, 16, 32, 48}
     std::vector<int64_t> unit_full, unit_coarse, unit_fine, unit_list, wtile;
     std::vector<Wave> waves;
     size_t pair_smem = 0;
@@ -190,7 +190,7 @@ inline unsigned long long* best_keys(cp_plan_t p) { return p->d_u64 + 1; }
 inline unsigned long long* queue_word(cp_plan_t p, int i) { return p->d_u64 + 1 + p->n_curves + i; }
 constexpr int kQueuesPerWave = 4;   // one work counter per (wave, stage)
 
-constexpr int kCoefStride = 32;   // a_1..a_32 stored per curve (largest class)
+constexpr int kCoefStride = kTcMaxHarmonics;   // a_1..a_48 stored per curve (largest class)
 
 int class_rank(int cls)
 {
@@ -200,6 +200,7 @@ int class_rank(int cls)
     case 12: return 3;
     case 16: return 4;
     case 32: return 5;
+    case 48: return 6;
     }
     return 0;   // direct form
 }
@@ -208,22 +209,23 @@ int class_rank(int cls)
 // series, relative to its peak value 1.
 double harmonic_tail(double sigma_t, int n)
 {
-    double a[33];
-    if (cp_bessel_coefficients(sigma_t, n, a) != CP_OK) return 1.0;
+    double a[kTcMaxHarmonics + 1];
+    if (n > kTcMaxHarmonics || cp_bessel_coefficients(sigma_t, n, a) != CP_OK) return 1.0;
     double s = 0.0;
     for (int k = 0; k <= n; k++) s += a[k];
     return 1.0 - s;
 }
 
-// Smallest harmonic count of the tensor form (8, 12, 16, 32) whose truncation
-// tail stays below 1e-4 of the kernel peak; 0 (direct form) when even 32 harmonics do
-// not reach it (sigma_t below about 0.13).  The tail falls as sigma_t grows,
-// so each class is a threshold on sigma_t, found once by bisection.
+// Smallest harmonic count of the tensor form (8, 12, 16, 32, 48) whose
+// truncation tail stays below 1e-4 of the kernel peak; 0 (direct form) when even
+// 48 harmonics do not reach it (sigma_t below about 0.09, which the sigma_t rule
+// never gives).  The tail falls as sigma_t grows, so each class is a threshold
+// on sigma_t, found once by bisection.
 const std::vector<double>& harmonic_thresholds()
 {
     static const std::vector<double> thr = [] {
         std::vector<double> t;
-        for (int n : {8, 12, 16, 32}) {
+        for (int n : {8, 12, 16, 32, 48}) {
             double lo = 0.02, hi = 4.0;
             for (int it = 0; it < 40; it++) {
                 const double mid = 0.5 * (lo + hi);
@@ -242,8 +244,8 @@ static bool w_bf16(int dtype) { return dtype == CP_DTYPE_BF16 || dtype == CP_DTY
 int harmonics_for(float sigma_t)
 {
     const std::vector<double>& thr = harmonic_thresholds();
-    const int cls[4] = {8, 12, 16, 32};
-    for (int k = 0; k < 4; k++)
+    const int cls[5] = {8, 12, 16, 32, 48};
+    for (int k = 0; k < 5; k++)
         if ((double)sigma_t >= thr[k]) return cls[k];
     return 0;
 }
@@ -253,7 +255,7 @@ int harmonics_for(float sigma_t)
 float sigma_t_floor(int cls)
 {
     const std::vector<double>& thr = harmonic_thresholds();
-    const int k = cls == 8 ? 0 : cls == 12 ? 1 : cls == 16 ? 2 : cls == 32 ? 3 : -1;
+    const int k = cls == 8 ? 0 : cls == 12 ? 1 : cls == 16 ? 2 : cls == 32 ? 3 : cls == 48 ? 4 : -1;
     if (k < 0) return 0.f;
     float f = (float)thr[k];
     if ((double)f < thr[k]) f = std::nextafter(f, INFINITY);   // the first FP32 value harmonics_for accepts
@@ -426,7 +428,11 @@ cp_status enqueue_stats(cp_plan_t p, cudaStream_t s)
     a.wrho = p->tensor ? p->d_wrho : nullptr;
     a.wrho_bf16 = w_bf16(p->opt.dtype) ? 1 : 0;
     CP_CUDA(launch_stats(a, (int)p->n_curves, s));
-    if (p->tensor) CP_CUDA(launch_harmonic_coef(p->d_cp, (int)p->n_curves, kCoefStride, p->d_coef, s));
+    if (p->tensor) {
+        // coefficients up to the plan's largest class (the quadrature size follows the count)
+        const int count = p->class_count[class_rank(48)] ? 48 : 32;
+        CP_CUDA(launch_harmonic_coef(p->d_cp, (int)p->n_curves, count, kCoefStride, p->d_coef, s));
+    }
     return CP_OK;
 }
 
@@ -801,10 +807,10 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
         if (opt.dtype != CP_DTYPE_FP16 && opt.dtype != CP_DTYPE_BF16 && opt.dtype != CP_DTYPE_BF16_SPLIT)
             return fail(CP_EINVAL, "cp_plan: dtype must be CP_DTYPE_FP16, CP_DTYPE_BF16 or CP_DTYPE_BF16_SPLIT");
         if (opt.n_max != 0 && opt.n_max != 4 && opt.n_max != 8 && opt.n_max != 12 && opt.n_max != 16 &&
-            opt.n_max != 32)
-            return fail(CP_EINVAL, "cp_plan: n_max must be 0 (per curve), 4, 8, 12, 16 or 32");
-        if (opt.dtype == CP_DTYPE_BF16_SPLIT && opt.n_max == 12)
-            return fail(CP_EINVAL, "cp_plan: n_max 12 is not available with CP_DTYPE_BF16_SPLIT (4, 8, 16 or 32)");
+            opt.n_max != 32 && opt.n_max != 48)
+            return fail(CP_EINVAL, "cp_plan: n_max must be 0 (per curve), 4, 8, 12, 16, 32 or 48");
+        if (opt.dtype == CP_DTYPE_BF16_SPLIT && (opt.n_max == 12 || opt.n_max == 48))
+            return fail(CP_EINVAL, "cp_plan: n_max 12 and 48 are not available with CP_DTYPE_BF16_SPLIT (4, 8, 16 or 32)");
         p->tensor = true;
         p->n_max = opt.n_max;
         // test hook: shorter bounded waits, to exercise the timeout path
@@ -831,8 +837,8 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
                 return fail(CP_EINVAL, "cp_plan: tuning.bucket_max_n must be >= 2 and strictly ascending");
             if (fc != 2 && fc != 4 && fc != 8 && fc != 16)
                 return fail(CP_EINVAL, "cp_plan: tuning.direct_fc must be 2, 4, 8 or 16");
-            if (tune.tensor_classes[b] < 0 || tune.tensor_classes[b] > 15)
-                return fail(CP_EINVAL, "cp_plan: tuning.tensor_classes must be a 4-bit mask");
+            if (tune.tensor_classes[b] < 0 || tune.tensor_classes[b] > 31)
+                return fail(CP_EINVAL, "cp_plan: tuning.tensor_classes must be a 5-bit mask");
         }
         opt.tuning = nullptr;   // copied; the caller's struct is not kept
         p->tune = tune;
@@ -974,8 +980,9 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             for (int64_t c = 0; c < n_curves; c++) {
                 int cl = harmonics_for(st[c]);
                 if (cl == 12 && opt.dtype == CP_DTYPE_BF16_SPLIT) cl = 16;   // no 12-harmonic split-Z class
+                if (cl == 48 && opt.dtype == CP_DTYPE_BF16_SPLIT) cl = 0;    // nor a 48-harmonic one
                 const int tb = tune_bucket(tune, (int)(offsets[c + 1] - offsets[c]));
-                const int bit = cl == 8 ? 1 : cl == 16 ? 2 : cl == 32 ? 4 : cl == 12 ? 8 : 0;
+                const int bit = cl == 8 ? 1 : cl == 16 ? 2 : cl == 32 ? 4 : cl == 12 ? 8 : cl == 48 ? 16 : 0;
                 if (tb >= 0 && bit && !(tune.tensor_classes[tb] & bit)) cl = 0;   // tuned: direct form is faster here
                 p->cls[c] = cl;
             }
@@ -1186,7 +1193,7 @@ static cp_status plan_impl(const double* times, const float* mags, const float* 
             return fail(CP_EUNSUPPORTED, "cp_plan: spectral-window buffers do not fit in shared memory");
         CP_CUDA(prepare_bands_kernels(p->np2max, p->max_band_points, g.trials_per_band));
     }
-    for (int nm : {4, 8, 12, 16, 32})
+    for (int nm : {4, 8, 12, 16, 32, 48})
         if (p->class_count[class_rank(nm)]) CP_CUDA(prepare_tensor_kernel(nm));   // one CTA per SM
     {
         int occ = 1;
@@ -1433,7 +1440,7 @@ cp_status cp_get_plan_info(cp_plan_t p, cp_plan_info* info)
     info->last_step_ms = p->last_step_ms;
     info->n_sm = p->n_sm;
     info->max_n = p->max_n;
-    for (int k = 0; k < 6; k++) info->class_curves[k] = p->class_count[k];
+    for (int k = 0; k < 7; k++) info->class_curves[k] = p->class_count[k];
     info->last_tensor_kernel_ms = p->last_tensor_ms;
     info->last_direct_kernel_ms = p->last_direct_ms;
     info->tensor_flops_search = p->tensor_flops;

@@ -315,11 +315,14 @@ cudaError_t launch_window(const WindowArgs& a, cudaStream_t s);
 
 size_t tensor_smem_bytes(bool bf16);
 size_t tensor_tile_bytes(bool bf16);   // bytes of one stored W' tile (BF16: hi and lo parts)
+// Largest harmonic count of the tensor form (the coefficient arrays hold this many per curve).
+constexpr int kTcMaxHarmonics = 48;
 int tensor_tiles_of(int n);
 int tensor_freqs_per_unit(int n_max, bool zsplit);
 cudaError_t prepare_tensor_kernel(int n_max);
 cudaError_t launch_build_w16(const BuildW16Args& a, cudaStream_t s);
-cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max, float* coef, cudaStream_t s);
+cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max, int stride, float* coef,
+                                 cudaStream_t s);
 cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s);
 
 // Launchers (cp_kernels.cu); return the launch error.

@@ -76,12 +76,13 @@ __host__ __device__ constexpr int tc_ft(int nmax, bool zs) { return tc_cols_h(zs
 __host__ __device__ constexpr int tc_ew(int nmax, bool zs) { return nmax <= 16 && (tc_ft(nmax, zs) / 2) % 2 == 0 ? 8 : 4; }
 // Producer items split a frequency's harmonics into this many ranges for 32
 // harmonics (4 frequencies per unit): 64 items per stage instead of 32, so
-// three stages are produced by 192 threads instead of 96.
+// three stages are produced by 192 threads instead of 96; 48 harmonics (2
+// frequencies per unit, 192 columns): three ranges of 16.
 // With split Z a unit has half the frequencies, so the harmonic ranges are
 // halved too (8 and 16 harmonics: 2 ranges, 32: 4) to keep the items per stage.
 __host__ __device__ constexpr int tc_hsplit(int nmax, bool zs)
 {
-    return zs ? (nmax == 4 ? 1 : nmax == 32 ? 4 : 2) : (nmax == 32 ? 2 : 1);
+    return zs ? (nmax == 4 ? 1 : nmax == 32 ? 4 : 2) : (nmax == 32 ? 2 : nmax == 48 ? 3 : 1);
 }
 // Items of one Z stage: (j-octet, frequency, harmonic range).  A stage group
 // takes a whole number of warps: a warp split between two groups would run
@@ -211,11 +212,14 @@ __global__ void __launch_bounds__(256) k_build_w16(const BuildW16Args a)
 // trapezoid rule on (1/pi) int_0^pi e^{k(cos t - 1)} cos(n t) dt.  The
 // integrand is evaluated in FP32 (relative error ~1e-5 at most, from the
 // exponent's rounding at k <= 100 and n^2 2^-24 from the Chebyshev recurrence
-// for cos(n t); far below the tensor form's 1e-3), each lane sums its <= M/32
-// points in FP32, and the warp sum is FP64.  (FP64 transcendentals run at
-// 1.68 operations/clk/SM here; this took 0.4 ms per 4096 curves in FP64.)
+// for cos(n t), n <= 32; beyond 32, cos(n t) is evaluated directly on the
+// exactly reduced angle (n k mod 2M) / M turns of pi; far below the tensor
+// form's 1e-3), each lane sums its <= M/32 points in FP32, and the warp sum is
+// FP64.  (FP64 transcendentals run at 1.68 operations/clk/SM here; this took
+// 0.4 ms per 4096 curves in FP64.)  Written at coef[c * stride + n - 1].
 // ===========================================================================
-__global__ void __launch_bounds__(256) k_harmonic_coef(const CurveParams* cp, int n_curves, int n_max, float* coef)
+__global__ void __launch_bounds__(256) k_harmonic_coef(const CurveParams* cp, int n_curves, int n_max, int stride,
+                                                       float* coef)
 {
     const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -223,9 +227,9 @@ __global__ void __launch_bounds__(256) k_harmonic_coef(const CurveParams* cp, in
     const float st = cp[c].sigma_t;
     const float kap = 1.0f / (st * st);
     const int M = 64 + 4 * (int)kap + 4 * n_max;
-    float acc[32];
+    float acc[kTcMaxHarmonics];
 #pragma unroll
-    for (int q = 0; q < 32; q++) acc[q] = 0.f;
+    for (int q = 0; q < kTcMaxHarmonics; q++) acc[q] = 0.f;
     for (int k = lane; k <= M; k += 32) {
         float sn, ct;
         sincospif((float)k / (float)M, &sn, &ct);
@@ -239,13 +243,16 @@ __global__ void __launch_bounds__(256) k_harmonic_coef(const CurveParams* cp, in
             cm2 = cm1;
             cm1 = cn;
         }
+#pragma unroll
+        for (int q = 32; q < kTcMaxHarmonics; q++)
+            if (q < n_max) acc[q] = fmaf(e, cospif((float)(((q + 1) * k) % (2 * M)) / (float)M), acc[q]);
     }
 #pragma unroll
-    for (int q = 0; q < 32; q++) {
+    for (int q = 0; q < kTcMaxHarmonics; q++) {
         double v = (double)acc[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0 && q < n_max) coef[(int64_t)c * n_max + q] = (float)(2.0 * v / (double)M);
+        if (lane == 0 && q < n_max) coef[(int64_t)c * stride + q] = (float)(2.0 * v / (double)M);
     }
 }
 
@@ -991,6 +998,10 @@ cudaError_t prepare_tensor_kernel(int n_max)
         if (e == cudaSuccess) e = set_tensor_smem<32, true, false>();
         if (e == cudaSuccess) e = set_tensor_smem<32, true, true>();
         break;
+    case 48:
+        e = set_tensor_smem<48, false, false>();
+        if (e == cudaSuccess) e = set_tensor_smem<48, true, false>();
+        break;
     }
     return e;
 }
@@ -1005,9 +1016,11 @@ cudaError_t launch_build_w16(const BuildW16Args& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max, float* coef, cudaStream_t s)
+cudaError_t launch_harmonic_coef(const CurveParams* cp, int n_curves, int n_max, int stride, float* coef,
+                                 cudaStream_t s)
 {
-    k_harmonic_coef<<<(n_curves + 7) / 8, 256, 0, s>>>(cp, n_curves, n_max, coef);
+    if (n_max < 1 || n_max > kTcMaxHarmonics || stride < n_max) return cudaErrorInvalidValue;
+    k_harmonic_coef<<<(n_curves + 7) / 8, 256, 0, s>>>(cp, n_curves, n_max, stride, coef);
     return cudaGetLastError();
 }
 
@@ -1015,7 +1028,7 @@ cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s)
 {
     const bool bf = a.bf16 != 0, list = a.stage == kStageList, zs = a.zsplit != 0;
     const size_t b = tensor_smem_bytes(bf);
-    if (zs && (!bf || a.n_max == 12)) return cudaErrorInvalidValue;
+    if (zs && (!bf || a.n_max == 12 || a.n_max == 48)) return cudaErrorInvalidValue;
 #define CP_TC_GO(NM, BFV, LV, ZV) k_pair_tensor<NM, BFV, LV, ZV><<<grid, tc_threads(NM, ZV), b, s>>>(a)
 #define CP_TC_LAUNCH(NM, ZOK)                                                                   \
     case NM:                                                                                    \
@@ -1038,6 +1051,7 @@ cudaError_t launch_pair_tensor(const TensorArgs& a, int grid, cudaStream_t s)
         CP_TC_LAUNCH(12, false)
         CP_TC_LAUNCH(16, true)
         CP_TC_LAUNCH(32, true)
+        CP_TC_LAUNCH(48, false)
     default: return cudaErrorInvalidValue;
     }
 #undef CP_TC_LAUNCH

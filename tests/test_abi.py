@@ -111,12 +111,12 @@ def test_argument_validation_precedes_device_use():
     good = {"buckets": [{"max_n": 256, "direct_fc": 16, "tensor": {"8": True, "16": True, "32": False}},
                         {"max_n": 4096, "direct_fc": 4, "tensor": {}}]}
     t = cp.tuning_from(good)
-    assert t.n_buckets == 2 and list(t.tensor_classes[:2]) == [11, 15]   # bits: 8, 16, 32, 12 harmonics
+    assert t.n_buckets == 2 and list(t.tensor_classes[:2]) == [27, 31]   # bits: 8, 16, 32, 12, 48 harmonics
     bad_fc = cp.tuning_from(good); bad_fc.direct_fc[0] = 6
     assert _plan_status([0, 5], tuning=bad_fc) == cp.CP_EINVAL
     bad_order = cp.tuning_from(good); bad_order.bucket_max_n[1] = 100
     assert _plan_status([0, 5], tuning=bad_order) == cp.CP_EINVAL
-    bad_mask = cp.tuning_from(good); bad_mask.tensor_classes[0] = 16
+    bad_mask = cp.tuning_from(good); bad_mask.tensor_classes[0] = 32
     assert _plan_status([0, 5], tuning=bad_mask) == cp.CP_EINVAL
 
 
@@ -138,6 +138,7 @@ def test_tensor_operand_type_is_validated_before_device_use():
     assert _plan_status([0, 5], dtype=-1, **tensor) == cp.CP_EINVAL
     # split Z has no 12-harmonic class
     assert _plan_status([0, 5], dtype=cp.CP_DTYPE_BF16_SPLIT, n_max=12, **tensor) == cp.CP_EINVAL
+    assert _plan_status([0, 5], dtype=cp.CP_DTYPE_BF16_SPLIT, n_max=48, **tensor) == cp.CP_EINVAL
     assert _plan_status([0, 5], dtype=cp.CP_DTYPE_BF16, n_max=20, **tensor) == cp.CP_EINVAL
 
 

@@ -50,7 +50,7 @@ def random_case(seed):
     df = float(10.0 ** rng.uniform(-5, -2))
     n_freq = 1 if rng.uniform() < 0.1 else int(rng.integers(2, 701))
     g = synth.Grid(f_min, df, n_freq)
-    sigma_t = float(rng.uniform(0.12, 0.7))
+    sigma_t = float(rng.uniform(0.1, 0.7))   # 0.1: the sigma_t rule's floor (48 harmonics)
     return b, g, sigma_t
 
 

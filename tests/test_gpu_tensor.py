@@ -61,7 +61,7 @@ def ragged():
     return b, g, ref
 
 
-@pytest.mark.parametrize("n_max", [12, 16, 32])
+@pytest.mark.parametrize("n_max", [12, 16, 32, 48])
 def test_tensor_fp16_parity_ragged(ragged, n_max):
     b, g, ref = ragged
     out, best, _ = run(b, g, sigma_t=0.45, form=cp.CP_FORM_TENSOR, dtype=cp.CP_DTYPE_FP16, n_max=n_max)
@@ -69,6 +69,30 @@ def test_tensor_fp16_parity_ragged(ragged, n_max):
     err = peak_err(out, ref, rows)
     assert np.all(err <= TOL), err
     accept_best(best, ref, rows, TOL)
+
+
+@pytest.mark.parametrize("dtype,tol", [(cp.CP_DTYPE_FP16, TOL), (cp.CP_DTYPE_BF16, BF16_TOL)])
+def test_tensor_48_harmonics_at_the_smallest_sigma_t(dtype, tol):
+    """sigma_t = 0.1, the skewness rule's floor, needs 48 harmonics (tail
+    1.5e-6 of the kernel peak; 32 leave 1.2e-3): the 48-harmonic class meets
+    the tensor bar against the oracle on a ragged batch with a tail tile, and
+    the per-curve choice takes it."""
+    b = synth.ragged_batch(5, seed=41, n_lo=120, n_hi=700)
+    g = synth.Grid(0.01, 3e-4, 300)
+    st = float(np.float32(0.1))
+    ref = oracle.batch_nckp(b, np.full(b.n_curves, st), g.freqs())
+    rows = range(b.n_curves)
+    out, best, _ = run(b, g, sigma_t=0.1, form=cp.CP_FORM_TENSOR, dtype=dtype, n_max=48)
+    err = peak_err(out, ref, rows)
+    print("\n48 harmonics, sigma_t 0.1, dtype %d: per-curve peak-relative error" % dtype, " ".join("%.2e" % x for x in err))
+    assert np.all(err <= tol), err
+    accept_best(best, ref, rows, tol)
+    if dtype == cp.CP_DTYPE_FP16:
+        out32, _, _ = run(b, g, sigma_t=0.1, form=cp.CP_FORM_TENSOR, dtype=dtype, n_max=32)
+        assert peak_err(out32, ref, rows).max() > err.max()          # 32 harmonics truncate here
+    with cp.Plan(b.times, b.mags, b.errs, b.offsets, cp.grid_from(g), sigma_t=0.1, form=cp.CP_FORM_TENSOR,
+                 dtype=dtype, n_max=0) as p:
+        assert p.info()["class_curves"] == [0, 0, 0, 0, 0, 0, b.n_curves]
 
 
 def test_tensor_truncation_converges_with_n_max(ragged):
@@ -212,9 +236,10 @@ def test_bounded_waits_report_timeout_and_keep_context():
 
 
 def test_tensor_auto_harmonics_per_curve():
-    """n_max = 0 picks per curve the smallest of 8/12/16/32 harmonics whose
-    truncation tail is <= 1e-4; curves with sigma_t too small for 32 run in the
-    direct form.  Every curve must meet the tensor tolerance."""
+    """n_max = 0 picks per curve the smallest of 8/12/16/32/48 harmonics whose
+    truncation tail is <= 1e-4; 48 harmonics cover sigma_t down to 0.1, the
+    skewness rule's smallest value (with split Z those curves run in the direct
+    form).  Every curve must meet the tensor tolerance."""
     b = synth.ragged_batch(10, seed=33, n_lo=150, n_hi=600)
     st = np.array([0.1, 0.11, 0.13, 0.15, 0.2, 0.25, 0.3, 0.45, 0.55, 0.6], np.float32)
     g = synth.Grid(0.01, 2e-4, 700)
@@ -226,7 +251,7 @@ def test_tensor_auto_harmonics_per_curve():
         best = p.best_period()
         info = p.info()
     out = out.cpu().numpy()
-    assert info["class_curves"] == [2, 0, 2, 1, 2, 3]    # direct, 4, 8, 12, 16, 32 harmonics
+    assert info["class_curves"] == [0, 0, 2, 1, 2, 3, 2]    # direct, 4, 8, 12, 16, 32, 48 harmonics
     ref = oracle.batch_nckp(b, st.astype(np.float64), g.freqs())
     err = peak_err(out, ref, range(b.n_curves))
     assert np.all(err <= TOL), err
@@ -239,7 +264,7 @@ def test_tensor_auto_harmonics_per_curve():
         p.sync()
         best = p.best_period()
         info = p.info()
-    assert info["class_curves"] == [2, 0, 2, 0, 3, 3]
+    assert info["class_curves"] == [2, 0, 2, 0, 3, 3, 0]
     err = peak_err(out.cpu().numpy(), ref, range(b.n_curves))
     print("\nBF16 split, per-curve harmonics: per-curve peak-relative error", " ".join("%.2e" % x for x in err))
     assert np.all(err <= TOL), err
@@ -262,7 +287,7 @@ def test_tuning_table_moves_a_class_to_the_direct_form():
         info = p.info()
     small = int(np.sum(b.sizes <= 400))
     assert 0 < small < b.n_curves
-    assert info["class_curves"] == [small, 0, 0, 0, b.n_curves - small, 0]
+    assert info["class_curves"] == [small, 0, 0, 0, b.n_curves - small, 0, 0]
     ref = oracle.batch_nckp(b, st.astype(np.float64), g.freqs())
     err = peak_err(out.cpu().numpy(), ref, range(b.n_curves))
     assert np.all(err <= TOL), err
