@@ -271,6 +271,10 @@ __global__ void __launch_bounds__(kStatsThreads) k_sigma_t_rule(const float* mag
     if (tid == 0) out[c] = (float)sigma_t_rule(ys, n);
 }
 
+// Curves with sigma_t at or above this take the exponent in the cos form (see
+// pair_item); below it the sin form keeps the exponent's rounding relative.
+constexpr float kCosFormMinSigma = 0.3f;
+
 // ===========================================================================
 // k_build_w: one warp per 32x32 tile of the upper block triangle.
 // Layout per tile: [k][lane][m] floats, k < 8 rows, m < 4 columns per lane.
@@ -301,6 +305,10 @@ __global__ void __launch_bounds__(256) k_build_w(const BuildWArgs a)
     int bi, bj;
     decode_tile((int)(T - a.wtile_start[lo]), nb, bi, bj);
     const int la = lane >> 3, lb = lane & 7;
+    // cos-form curves: w carries the exponent's constant term, w 2^(-beta/2), so
+    // that the pair kernel's exponent is the bare product sum (see pair_item)
+    const float tsc = P.tscale * P.tscale * 0.70710678f;
+    const float wscale = P.sigma_t >= kCosFormMinSigma ? exp2f(-(tsc * tsc)) : 1.0f;
     float ypc[kColsPerLane];
     int jj[kColsPerLane];
 #pragma unroll
@@ -317,7 +325,7 @@ __global__ void __launch_bounds__(256) k_build_w(const BuildWArgs a)
 #pragma unroll
         for (int m = 0; m < kColsPerLane; m++) {
             const float g = gauss_g(ypr, ypc[m]);
-            w[m] = (i < jj[m] && jj[m] < n) ? (g - P.ip_hi) - P.ip_lo : 0.f;
+            w[m] = (i < jj[m] && jj[m] < n) ? ((g - P.ip_hi) - P.ip_lo) * wscale : 0.f;
         }
         reinterpret_cast<float4*>(dst)[k * 32 + lane] = make_float4(w[0], w[1], w[2], w[3]);
     }
@@ -334,9 +342,6 @@ constexpr int kPairThreads = 512;
 constexpr int kItemRows = 8;
 constexpr int kItemsPerTile = kRowsPerLane / kItemRows;
 constexpr bool kPrefetchW = kItemRows == 4;   // next item's W in registers (the half-tile item only)
-// Curves with sigma_t at or above this take the exponent in the cos form (see
-// pair_item); below it the sin form keeps the exponent's rounding relative.
-constexpr float kCosFormMinSigma = 0.3f;
 // The unit's trig table is built by one thread per (point, half of the
 // frequency pairs): each point's phase and step are loaded twice per unit
 // instead of once per frequency pair, and the threads' shares stay even
@@ -350,12 +355,16 @@ constexpr int kTableGroups = 2;
 //   sin form  -(c_i s_j - s_i c_j)^2 with (s, c) = (sin, cos)(pi phi) sqrt(beta)
 //             (three f32x2 operations per two frequencies);
 //   cos form  C_i C_j + S_i S_j - beta/2 with (S, C) = (sin, cos)(2 pi phi)
-//             sqrt(beta/2), from sin^2 x = (1 - cos 2x)/2 (two operations).
+//             sqrt(beta/2), from sin^2 x = (1 - cos 2x)/2; the constant
+//             2^(-beta/2) is carried by the tile's w (k_build_w), so the
+//             exponent is the bare sum, a multiply and an FMA (two operations,
+//             one of them with two operands).
 // The cos form's rounding is absolute, about beta 2^-24 in the exponent, so it
-// is used only for sigma_t >= kCosFormMinSigma (beta <= 32: below 3e-6 per term).
+// is used only for sigma_t >= kCosFormMinSigma (beta <= 32: below 3e-6 per term;
+// the exponent then lies in [-beta/2, beta/2], within FP32 range).
 template <bool COSF>
 __device__ __forceinline__ void pair_item(const ulonglong2* SC, const f2* NS, int npad, int nfp, int rbase,
-                                          int cbase, f2 nhalf, const f2 (&w01)[kItemRows],
+                                          int cbase, const f2 (&w01)[kItemRows],
                                           const f2 (&w23)[kItemRows], f2 (&acc)[kFcMax / 2])
 {
 #pragma unroll
@@ -375,7 +384,7 @@ __device__ __forceinline__ void pair_item(const ulonglong2* SC, const f2* NS, in
                     const ulonglong2 R = SCf[i];   // ((S_i(f), S_i(f')), (C_i(f), C_i(f')))
 #pragma unroll
                     for (int m = 0; m < kColsPerLane; m++) {
-                        const f2 a2 = fma2(R.y, col[m].y, fma2(R.x, col[m].x, nhalf));
+                        const f2 a2 = fma2(R.y, col[m].y, mul2(R.x, col[m].x));
                         float a0, a1;
                         upk(a2, a0, a1);
                         e[m][0] = ex2_approx(a0);
@@ -514,7 +523,6 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
         const int nitems = kItemsPerTile * ntiles;   // (tile, row part): 4 kItemRows x 32 pairs per warp item
         const float4* Wc = reinterpret_cast<const float4*>(a.W + (a.wtile_start[slot] - a.wtile_base) * kTileFloats);
         f2 acc[kFcMax / 2];                      // per f-pair: (sum at f, sum at f')
-        const f2 nhalf = pk(-ts * ts, -ts * ts);   // cos form: -beta/2
 #pragma unroll
         for (int q = 0; q < kFcMax / 2; q++) acc[q] = 0ull;
 
@@ -546,8 +554,8 @@ __global__ void __launch_bounds__(kPairThreads, 1) k_pair_direct(const PairArgs 
             decode_tile(item / kItemsPerTile, nb, bi, bj);
             const int rbase = bi * kTile + (item % kItemsPerTile) * (4 * kItemRows) + la;
             const int cbase = bj * kTile + lb;
-            if (cosf) pair_item<true>(SC, NS, npad, nfp, rbase, cbase, nhalf, w01, w23, acc);
-            else pair_item<false>(SC, NS, npad, nfp, rbase, cbase, nhalf, w01, w23, acc);
+            if (cosf) pair_item<true>(SC, NS, npad, nfp, rbase, cbase, w01, w23, acc);
+            else pair_item<false>(SC, NS, npad, nfp, rbase, cbase, w01, w23, acc);
         }
 
         // warp reduction of the 2*nfp frequency sums, then a fixed-order CTA sum
