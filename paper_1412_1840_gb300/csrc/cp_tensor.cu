@@ -226,7 +226,9 @@ __global__ void __launch_bounds__(256) k_harmonic_coef(const CurveParams* cp, in
     if (c >= n_curves) return;
     const float st = cp[c].sigma_t;
     const float kap = 1.0f / (st * st);
-    const int M = 64 + 4 * (int)kap + 4 * n_max;
+    // quadrature points: enough for the integrand's width ~1/sqrt(k) and the
+    // highest harmonic (k capped so that a tiny sigma_t cannot overflow M)
+    const int M = 64 + 4 * (int)fminf(kap, (float)(1 << 20)) + 4 * n_max;
     float acc[kTcMaxHarmonics];
 #pragma unroll
     for (int q = 0; q < kTcMaxHarmonics; q++) acc[q] = 0.f;
@@ -245,7 +247,8 @@ __global__ void __launch_bounds__(256) k_harmonic_coef(const CurveParams* cp, in
         }
 #pragma unroll
         for (int q = 32; q < kTcMaxHarmonics; q++)
-            if (q < n_max) acc[q] = fmaf(e, cospif((float)(((q + 1) * k) % (2 * M)) / (float)M), acc[q]);
+            if (q < n_max)
+                acc[q] = fmaf(e, cospif((float)(((int64_t)(q + 1) * k) % (2 * M)) / (float)M), acc[q]);
     }
 #pragma unroll
     for (int q = 0; q < kTcMaxHarmonics; q++) {
