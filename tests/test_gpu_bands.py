@@ -142,7 +142,8 @@ def test_bands_edge_batch():
             assert not oracle.is_one_day(g.f_min + k * g.df)
 
 
-@pytest.mark.parametrize("n_max,dtype", [(0, cp.CP_DTYPE_FP16), (16, cp.CP_DTYPE_FP16), (0, cp.CP_DTYPE_BF16_SPLIT)])
+@pytest.mark.parametrize("n_max,dtype", [(0, cp.CP_DTYPE_FP16), (16, cp.CP_DTYPE_FP16), (48, cp.CP_DTYPE_FP16),
+                                         (0, cp.CP_DTYPE_BF16_SPLIT)])
 def test_bands_tensor_form(small, n_max, dtype):
     b, g = small
     best_d, tr_d, _ = run(b, g, sigma_t=0.35)
